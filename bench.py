@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the R-SLB shock-tube step on GB300.
+
+Workload: the ultrarelativistic Sod shock tube at scale -- 65536 cells on
+[-1, 1], 3 x 200 velocities (Gauss-Laguerre x Gauss-Legendre), N_Omega = 5,
+CFL 0.5, outflow boundaries -- for each relaxation time tau in
+{1e-4, 1e-2, 1, 10}.  One bench step = one TVD-RK3 time step (three fused
+stage kernels) of each of the four tubes, FP32 populations with FP64 Landau
+matching.  Metric: cell-velocity updates per second.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank advances its own replica of the workload
+(the single-tube step has no exchange to shard), rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1612_01287_gb300 import workloads  # noqa: E402
+
+METRIC = "cell-velocity updates/s"
+UNIT = "cv-updates/s"
+TAUS = workloads.SOD_LARGE_TAUS
+FALLBACK_HBM_GBS = 6800.0
+BYTES_PER_CV_STEP_F32 = 32  # stage 1 r+w (8 B), stages 2-3 read f_n, f^(i), write (12 B each)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload_dt(w):
+    from paper_1612_01287_gb300 import quadrature
+    xi, _, _, _ = quadrature(w["Q_xi"], w["Q_L"])
+    return w["cfl"] * w["dz"] / float(np.abs(xi).max())
+
+
+def config_dict(w, dt):
+    return {"workload": "sod_shock_tube_Nx%d_NL%d_Nxi%d_tau{1e-4,1e-2,1,10}" % (
+        w["Z"], w["Q_L"], w["Q_xi"]),
+        "cells": w["Z"], "velocities": w["Q_L"] * w["Q_xi"], "N_Omega": w["N_Omega"],
+        "dt": dt, "cfl": w["cfl"], "tubes_per_step": len(TAUS), "bc": w["bc"],
+        "precision": "fp32 populations, fp64 Landau matching",
+        "l2": "inputs larger than L2 (157 MB per population buffer)"}
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- helpers
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1612_01287_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the last ncu capture, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path)).get(kernel)
+        if d and d.get("source_sha") == source_sha():
+            return d.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(w, dt, steps=20, cells=2048):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload:
+    `cells` cells around the membrane of one tube, all 600 velocities."""
+    import oracle
+    Z = w["Z"]
+    lo = Z // 2 - cells // 2
+    dz = w["dz"]
+    zc = -1.0 + (np.arange(lo, lo + cells) + 0.5) * dz
+    (nL, TL, bL), (nR, TR, bR) = w["left"], w["right"]
+    p = oracle.sod_params(cells, w["Q_xi"], w["Q_L"], w["N_Omega"], z_min=-1.0 + lo * dz,
+                          z_max=-1.0 + (lo + cells) * dz, bc="outflow", tau_mode="const",
+                          tau=1e-2, dt=dt)
+    f = oracle.sod_init_fields(p, np.where(zc < 0, nL, nR), np.where(zc < 0, TL, TR),
+                               np.where(zc < 0, bL, bR))
+    t0 = time.perf_counter()
+    oracle.sod_steps(p, f, steps)
+    el = time.perf_counter() - t0
+    cvu = cells * w["Q_xi"] * w["Q_L"] * steps
+    return {"value": cvu / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d cells x %d velocities x %d RK3 steps of one tube (tau=1e-2), "
+                      "single-threaded FP64 C oracle, %.1f s" % (cells, w["Q_xi"] * w["Q_L"],
+                                                                 steps, el)}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = workloads.sod_large()
+    from paper_1612_01287_gb300 import build
+    build.build()
+    dt = workload_dt(w)
+    # each step: the oracle advances a bounded sample by one RK3 step
+    import oracle
+    cells = 512
+    Z = w["Z"]
+    lo = Z // 2 - cells // 2
+    dz = w["dz"]
+    zc = -1.0 + (np.arange(lo, lo + cells) + 0.5) * dz
+    (nL, TL, bL), (nR, TR, bR) = w["left"], w["right"]
+    p = oracle.sod_params(cells, w["Q_xi"], w["Q_L"], w["N_Omega"], z_min=-1.0 + lo * dz,
+                          z_max=-1.0 + (lo + cells) * dz, bc="outflow", tau_mode="const",
+                          tau=1e-2, dt=dt)
+    f = oracle.sod_init_fields(p, np.where(zc < 0, nL, nR), np.where(zc < 0, TL, TR),
+                               np.where(zc < 0, bL, bR))
+    for _ in range(args.warmup):
+        f = oracle.sod_steps(p, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.sod_steps(p, f, 1)
+    el = time.perf_counter() - t0
+    cvu = cells * w["Q_xi"] * w["Q_L"] * args.steps
+    val = cvu / el
+    sample = ("%d cells x %d velocities per step, one RK3 step per bench step, "
+              "single-threaded FP64 C oracle" % (cells, w["Q_xi"] * w["Q_L"]))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(w, dt),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1612_01287_gb300 import Sod, build
+    torch.cuda.set_device(local_rank)
+    build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    w = workloads.sod_large()
+    dt = workload_dt(w)
+    stream = torch.cuda.current_stream()
+    tubes = [Sod(Z=w["Z"], Q_xi=w["Q_xi"], Q_L=w["Q_L"], N_Omega=w["N_Omega"], bc=w["bc"],
+                 tau=tau, dt=dt, left=w["left"], right=w["right"], precision="f32",
+                 stream=stream) for tau in TAUS]
+    V, Z = w["Q_xi"] * w["Q_L"], w["Z"]
+    cv_per_step = V * Z * len(TAUS)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        for t in tubes:
+            t.step(1)
+    barrier()
+    # per-launch timing of the stage kernels: one event pair per tube-step
+    nev = args.steps * len(TAUS)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(nev + 1)]
+    clk = ClockSampler(local_rank)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    ev[0].record(stream)
+    i = 0
+    for _ in range(args.steps):
+        for t in tubes:
+            t.step(1)
+            i += 1
+            ev[i].record(stream)
+    end.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = start.elapsed_time(end)
+    per_tube_step_ms = [ev[j].elapsed_time(ev[j + 1]) for j in range(nev)]
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    for t in tubes:
+        t.sync()
+
+    # ---- end to end through the C ABI with host buffers ----
+    import ctypes
+    tube = tubes[0]
+    nbytes = V * Z * 4
+    host_f = torch.empty(V * Z, dtype=torch.float32).pin_memory()
+    host_f.copy_(torch.from_numpy(tube.get_state().reshape(-1)))
+    host_m = torch.empty(14 * Z, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        tube.set_state_ptr(host_f.data_ptr(), 0)
+        tube.step(1)
+        tube.moments_into(host_m.data_ptr())
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_val = world * V * Z * e2e_steps / e2e_s
+
+    # ---- FP64 path, one tube, a few steps (ALU-bound on this part) ----
+    fp64 = None
+    if rank == 0:
+        with Sod(Z=w["Z"], Q_xi=w["Q_xi"], Q_L=w["Q_L"], N_Omega=w["N_Omega"], bc=w["bc"],
+                 tau=1e-2, dt=dt, left=w["left"], right=w["right"], precision="f64",
+                 stream=stream) as t64:
+            t64.step(1)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            t64.step(2)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fms = a.elapsed_time(b) / 2
+            fp64 = {"value": V * Z / (fms * 1e-3), "unit": UNIT, "ms_per_tube_step": fms,
+                    "note": "one tube, FP64 everywhere; bound by the FP64 pipe, not HBM"}
+
+    for t in tubes:
+        t.close()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    value = world * cv_per_step * args.steps / (ms * 1e-3)
+    per_launch_ms = statistics.mean(per_tube_step_ms) / 3.0
+    peak, peak_kind = measured_peak()
+    achieved = BYTES_PER_CV_STEP_F32 / 3.0 * V * Z / (per_launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(w, dt),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "kernel": "sod_stage_kernel<float,32>",
+                     "algorithmic_bytes_per_launch": BYTES_PER_CV_STEP_F32 / 3.0 * V * Z,
+                     "avg_launch_ms": per_launch_ms,
+                     "traffic": recorded_traffic("sod_stage_kernel<float,32>")},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": 14 * Z * 8, "steps": e2e_steps,
+                "note": "per step: pinned host populations -> device (rslb_set_state), one "
+                        "RK3 step (rslb_step), 14 fields -> pinned host (rslb_moments)"},
+        "gpu_launches": 3 * len(TAUS) * args.steps,
+        "clocks": clocks,
+        "fp64": fp64,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, dt)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+"""ctypes binding of the R-SLB C ABI (include/rslb.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``_build/librslb.so``.  The library must have been built (``build.build()``);
+importing the binding without it raises immediately -- there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FIELDS = ("n", "E", "P", "T", "beta", "gamma", "lambda_bar", "q", "Pi",
+          "Nt", "Nz", "Ttt", "Ttz", "Tzz")
+
+OK = 0
+ERR = {1: "RSLB_ERR_ARG", 2: "RSLB_ERR_CFL", 3: "RSLB_ERR_STIFF", 4: "RSLB_ERR_ALLOC",
+       5: "RSLB_ERR_CUDA", 6: "RSLB_ERR_NONPHYSICAL", 7: "RSLB_ERR_UNSUPPORTED"}
+F32, F64 = 0, 1
+BC = {"fixed_eq": 0, "outflow": 1, "periodic": 2}
+TAU = {"const": 0, "etas": 1, "none": 2}
+
+
+class RslbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (ERR.get(code, "error %d" % code), msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    """Mirror of ``rslb_config``."""
+    _fields_ = [("Z", ctypes.c_int), ("z_min", ctypes.c_double), ("z_max", ctypes.c_double),
+                ("Q_xi", ctypes.c_int), ("Q_L", ctypes.c_int), ("N_Omega", ctypes.c_int),
+                ("precision", ctypes.c_int), ("bc", ctypes.c_int), ("tau_mode", ctypes.c_int),
+                ("tau", ctypes.c_double), ("tau_AW0", ctypes.c_double),
+                ("lambda_ref", ctypes.c_double), ("dt", ctypes.c_double),
+                ("nL", ctypes.c_double), ("TL", ctypes.c_double), ("betaL", ctypes.c_double),
+                ("nR", ctypes.c_double), ("TR", ctypes.c_double), ("betaR", ctypes.c_double),
+                ("n0", ctypes.c_void_p), ("T0", ctypes.c_void_p), ("beta0", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB_PATH
+
+
+def load():
+    """Load the built library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("R-SLB CUDA library not built (%s missing); run "
+                           "paper_1612_01287_gb300.build.build() first" % path)
+    L = ctypes.CDLL(path)
+    i, p, d = ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+    sig = {
+        "rslb_quadrature": (i, [i, i, p, p, p, p]),
+        "rslb_init": (i, [ctypes.POINTER(p), ctypes.POINTER(Config), p]),
+        "rslb_step": (i, [p, i]),
+        "rslb_sync": (i, [p]),
+        "rslb_moments": (i, [p, p, i]),
+        "rslb_get_state": (i, [p, p, i]),
+        "rslb_set_state": (i, [p, p, i]),
+        "rslb_time": (i, [p, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),
+        "rslb_destroy": (None, [p]),
+        "rslb_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != OK:
+        msg = load().rslb_last_error()
+        raise RslbError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def quadrature(Q_xi, Q_L):
+    """(xi, w_xi, x_k, w_L) from ``rslb_quadrature``."""
+    xi, wx = np.zeros(Q_xi), np.zeros(Q_xi)
+    xk, wk = np.zeros(Q_L), np.zeros(Q_L)
+    _check(load().rslb_quadrature(int(Q_xi), int(Q_L), _ptr(xi), _ptr(wx), _ptr(xk), _ptr(wk)))
+    return xi, wx, xk, wk
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Sod:
+    """One Sod shock-tube simulation on the current CUDA device (``rslb_handle``)."""
+
+    def __init__(self, Z, Q_xi, Q_L=3, N_Omega=None, z_min=-1.0, z_max=1.0, precision="f32",
+                 bc="outflow", tau_mode="const", tau=1e-3, tau_AW0=0.0, lambda_ref=1.0, dt=5e-4,
+                 left=(1.0, 1.0, 0.0), right=(0.125, 0.8, 0.0), fields=None, stream=None):
+        """left/right: (n, T, beta); fields: optional (n0, T0, beta0) arrays of length Z."""
+        if N_Omega is None:
+            N_Omega = min(Q_xi - 1, 5)
+        self.Z, self.Q_xi, self.Q_L = int(Z), int(Q_xi), int(Q_L)
+        self.V = self.Q_xi * self.Q_L
+        if precision not in ("f32", "fp32", "f64", "fp64", F32, F64):
+            raise ValueError("precision must be 'f32' or 'f64'")
+        self.fp64 = precision in ("f64", "fp64", F64)
+        self.dtype = np.float64 if self.fp64 else np.float32
+        self._keep = None
+        cfg = Config(self.Z, z_min, z_max, self.Q_xi, self.Q_L, int(N_Omega),
+                     F64 if self.fp64 else F32, BC[bc] if isinstance(bc, str) else int(bc),
+                     TAU[tau_mode] if isinstance(tau_mode, str) else int(tau_mode),
+                     tau, tau_AW0, lambda_ref, dt, left[0], left[1], left[2],
+                     right[0], right[1], right[2], None, None, None)
+        if fields is not None:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in fields]
+            self._keep = arrs
+            cfg.n0, cfg.T0, cfg.beta0 = (a.ctypes.data for a in arrs)
+        self._h = ctypes.c_void_p()
+        self._stream = _stream_ptr(stream)
+        _check(load().rslb_init(ctypes.byref(self._h), ctypes.byref(cfg), self._stream))
+        self._keep = None
+
+    def step(self, nsteps=1):
+        _check(load().rslb_step(self._h, int(nsteps)))
+
+    def sync(self):
+        _check(load().rslb_sync(self._h))
+
+    def moments(self, out=None):
+        """Dict of FP64 numpy arrays (host) -- or fill a device buffer if ``out`` is a
+        CUDA torch tensor of shape (14, Z)."""
+        if out is not None:
+            _check(load().rslb_moments(self._h, ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        buf = np.zeros((len(FIELDS), self.Z))
+        _check(load().rslb_moments(self._h, _ptr(buf), 0))
+        return {k: buf[i] for i, k in enumerate(FIELDS)}
+
+    def moments_into(self, host_buf):
+        """Fill a caller-owned host array (14*Z doubles, e.g. pinned memory)."""
+        _check(load().rslb_moments(self._h, ctypes.c_void_p(host_buf), 0))
+
+    def get_state(self):
+        """Populations as a (V, Z) array of the handle's precision."""
+        f = np.zeros((self.V, self.Z), dtype=self.dtype)
+        _check(load().rslb_get_state(self._h, _ptr(f), 0))
+        return f
+
+    def set_state(self, f):
+        f = np.ascontiguousarray(f, dtype=self.dtype)
+        assert f.shape == (self.V, self.Z)
+        _check(load().rslb_set_state(self._h, _ptr(f), 0))
+        self.sync()
+
+    def set_state_ptr(self, ptr, on_device):
+        """Stream-ordered copy from a raw pointer (host pinned or device)."""
+        _check(load().rslb_set_state(self._h, ctypes.c_void_p(ptr), int(on_device)))
+
+    def time(self):
+        t = ctypes.c_double()
+        n = ctypes.c_longlong()
+        _check(load().rslb_time(self._h, ctypes.byref(t), ctypes.byref(n)))
+        return t.value, n.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().rslb_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

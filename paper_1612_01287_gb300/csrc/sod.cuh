@@ -1,0 +1,74 @@
+// sod.cuh -- host-visible declarations of the Sod shock-tube kernels.
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+namespace rslb {
+
+enum { kBcFixedEq = 0, kBcOutflow = 1, kBcPeriodic = 2 };
+enum { kTauConst = 0, kTauEtas = 1, kTauNone = 2 };
+
+struct SodGeom {
+  int Z;     // interior cells
+  int ldz;   // row pitch (elements) of a population buffer, >= Z
+  int V;     // velocities Q_xi * Q_L
+  int Qx, QL;
+  int nm;    // N_Omega + 1
+  int bc, tau_mode;
+  double inv_dz, dt, tau, tau_AW0, lambda_ref;
+};
+
+// Per-velocity tables in the working precision (device pointers).
+template <typename T>
+struct SodTables {
+  const T* mw;      // [5][V]: 1+xi, 1-xi, p(1+xi)^2, p(1-xi)^2, p(1-xi^2)
+  const T* xi;      // [V]
+  const T* wp;      // [kMaxM][V]: w_j w_k P_m(xi_j)
+  const int* kidx;  // [V]
+  const T* L1k;     // [QL]: L_1^{(2)}(x_k) = 3 - x_k
+  const T* ghostL;  // [V] fixed-equilibrium ghost populations
+  const T* ghostR;  // [V]
+  const double* gl_t;  // [kAeqNodes] Gauss-Legendre nodes on [-1, 1]
+  const double* gl_w;  // [kAeqNodes]
+};
+
+// FP64 tables used by the initialisation and moment kernels.
+struct SodTablesF64 {
+  const double* xi;   // [V]
+  const double* p;    // [V] p_k of row v
+  const double* wp;   // [kMaxM][V]
+  const int* kidx;    // [V]
+  const double* L1k;  // [QL]
+  const double* gl_t;
+  const double* gl_w;
+};
+
+// Tile shape chosen for a given precision and velocity count.
+struct SodLaunch {
+  int B;        // cells per CTA
+  size_t smem;  // dynamic shared memory bytes
+};
+
+// Pick the tile width for V velocities; returns B = 0 if V does not fit.
+SodLaunch sod_pick_launch(bool fp64, int V, int QL, int max_smem);
+
+// Enqueue one RK stage (stage = 0, 1, 2): fout = stage update of fin (and fn).
+template <typename T>
+cudaError_t sod_stage_launch(const SodLaunch& L, const SodGeom& g, const SodTables<T>& tb,
+                             const T* fin, const T* fn, T* fout, int stage, int* err,
+                             cudaStream_t st);
+
+// Per-cell coefficients c''_{k,m} (FP64) of f^eq for given (n, T, beta) per
+// cell, then populations f[v*ldz + s] = sum_m c''_{k(v),m}(s) wp_m(v).
+template <typename T>
+cudaError_t sod_init_launch(const SodGeom& g, const SodTablesF64& tb, const double* n,
+                            const double* Tt, const double* beta, double* coef_scratch, T* f,
+                            int* err, cudaStream_t st);
+
+// 14 FP64 fields per cell (rslb.h order), out[field*Z + s].
+template <typename T>
+cudaError_t sod_moments_launch(const SodGeom& g, const SodTablesF64& tb, const T* f,
+                               double* out, int* err, cudaStream_t st);
+
+}  // namespace rslb

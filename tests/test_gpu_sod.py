@@ -1,0 +1,190 @@
+"""GPU parity of the Sod shock-tube path against the FP64 oracle.
+
+Tolerances: the FP64 path must match to 1e-12 and the FP32 path to 1e-5 in
+the max-normalised error max_s|a-b|/max_s|b| on n, E, beta and Pi (the shear
+stress of Eq. pi_val); FP64 populations are also compared element by element.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_01287_gb300 import workloads
+from tests import sodcase
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_01287_gb300 import build, load
+    build.build()
+    load()
+
+
+def small_case():
+    w = workloads.sod_small()
+    w.pop("t_end")
+    return w
+
+
+def test_small_workload_full_run_fp64():
+    """The 256-cell, 60-velocity shock tube to t = 0.8 (1600 steps)."""
+    errs = sodcase.compare(small_case(), 1600, "f64", TOL64, TOL64)
+    print("fp64 full run errors", errs)
+
+
+def test_small_workload_fp32():
+    errs = sodcase.compare(small_case(), 400, "f32", TOL32)
+    print("fp32 400-step errors", errs)
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", TOL64), ("f32", TOL32)])
+def test_ragged_fixed_eq_odd_qxi(precision, tol):
+    """Z not a multiple of the tile, fixed-equilibrium ghosts, odd Q_xi (a xi = 0
+    node), Q_L = 2 as in the paper, N_Omega = 3."""
+    case = dict(Z=100, Q_xi=7, Q_L=2, N_Omega=3, bc="fixed_eq", tau=2e-3, dt=1e-3,
+                z_min=-0.5, z_max=0.5, left=(1.0, 1.0, 0.0), right=(0.125, 0.5, 0.0))
+    sodcase.compare(case, 60, precision, tol, tol if precision == "f64" else None)
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", TOL64), ("f32", TOL32)])
+def test_periodic_etas_smooth_flow(precision, tol):
+    """Periodic domain, smooth moving state, the eta/s relaxation-time law."""
+    Z = 64
+    case = dict(Z=Z, Q_xi=12, Q_L=3, N_Omega=5, bc="periodic", tau_mode="etas", tau_AW0=4e-3,
+                lambda_ref=1.0, dt=2e-3, z_min=0.0, z_max=1.0,
+                fields=workloads.random_smooth_fields(Z))
+    sodcase.compare(case, 40, precision, tol, tol if precision == "f64" else None)
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", TOL64), ("f32", TOL32)])
+def test_collisionless(precision, tol):
+    case = dict(Z=80, Q_xi=10, Q_L=2, bc="fixed_eq", tau_mode="none", dt=5e-3, z_min=-0.5,
+                z_max=0.5, left=(1.0, 1.0, 0.0), right=(0.125, 0.5, 0.0))
+    sodcase.compare(case, 40, precision, tol, tol if precision == "f64" else None)
+
+
+@pytest.mark.parametrize("Q_xi,Q_L", [(4, 2), (20, 3), (50, 3)])
+def test_small_velocity_sets_segmented_rows(Q_xi, Q_L):
+    """V = 8, 60, 150: rows split into segments across threads."""
+    case = dict(Z=96, Q_xi=Q_xi, Q_L=Q_L, N_Omega=min(Q_xi - 1, 5), bc="outflow", tau=1e-3,
+                dt=5e-4, left=(1.0, 1.0, 0.0), right=(0.125, 0.8, 0.0))
+    sodcase.compare(case, 30, "f64", TOL64, TOL64)
+
+
+@pytest.mark.parametrize("Z", [1, 2, 3, 33])
+def test_tiny_domains(Z):
+    case = dict(Z=Z, Q_xi=6, Q_L=2, bc="outflow", tau=1e-2, dt=2e-3, z_min=-1.0, z_max=1.0,
+                left=(1.0, 1.0, 0.0), right=(0.125, 0.8, 0.0))
+    sodcase.compare(case, 10, "f64", TOL64, TOL64)
+
+
+@pytest.mark.parametrize("precision,tol,Q_xi", [("f64", TOL64, 200), ("f32", TOL32, 200),
+                                                ("f64", TOL64, 300), ("f32", TOL32, 300)])
+def test_large_velocity_sets(precision, tol, Q_xi):
+    """V = 600 (the large workload) and V = 900 (narrower tiles)."""
+    case = dict(Z=48, Q_xi=Q_xi, Q_L=3, N_Omega=5, bc="outflow", tau=1e-2, dt=1e-3,
+                left=(1.0, 1.0, 0.0), right=(0.125, 0.8, 0.0))
+    sodcase.compare(case, 6, precision, tol, tol if precision == "f64" else None)
+
+
+def test_moving_states_negative_beta_fp64():
+    """Boosted initial states (sgn(beta) enters f^eq through P_m(sgn(beta) xi))."""
+    case = dict(Z=64, Q_xi=16, Q_L=3, N_Omega=6, bc="fixed_eq", tau=5e-3, dt=1e-3,
+                left=(0.8, 1.2, 0.5), right=(0.3, 0.7, -0.6))
+    sodcase.compare(case, 40, "f64", TOL64, TOL64)
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", TOL64), ("f32", TOL32)])
+def test_full_size_sampled_cells(precision, tol):
+    """65536 cells x 600 velocities (the benchmark launch): two steps on the GPU;
+    sampled cells are recomputed by the oracle on a window wide enough that its
+    own boundaries cannot reach the sample (each RK stage reaches 3 cells)."""
+    from paper_1612_01287_gb300 import Sod
+    w = workloads.sod_large(tau=1e-2)
+    Z, dz = w["Z"], w["dz"]
+    xi, _, _, _ = __import__("paper_1612_01287_gb300").quadrature(w["Q_xi"], w["Q_L"])
+    dt = w["cfl"] * dz / np.abs(xi).max()
+    steps = 2
+    with Sod(Z=Z, Q_xi=w["Q_xi"], Q_L=w["Q_L"], N_Omega=w["N_Omega"], bc=w["bc"], tau=w["tau"],
+             dt=dt, left=w["left"], right=w["right"], precision=precision) as s:
+        s.step(steps)
+        mg = s.moments()
+    R = 9 * steps + 6
+    rng = np.random.default_rng(7)
+    samples = sorted(set([0, 1, Z // 2 - 2, Z // 2 - 1, Z // 2, Z // 2 + 1, Z - 1]
+                         + list(rng.integers(0, Z, size=3))))
+    got = {k: [] for k in sodcase.PARITY_FIELDS}
+    ref = {k: [] for k in sodcase.PARITY_FIELDS}
+    nL, TL, bL = w["left"]
+    nR, TR, bR = w["right"]
+    for s0 in samples:
+        lo, hi = max(0, s0 - R), min(Z, s0 + R + 1)
+        zc = -1.0 + (np.arange(lo, hi) + 0.5) * dz
+        fields = (np.where(zc < 0, nL, nR), np.where(zc < 0, TL, TR), np.where(zc < 0, bL, bR))
+        case = dict(Z=hi - lo, Q_xi=w["Q_xi"], Q_L=w["Q_L"], N_Omega=w["N_Omega"], bc="outflow",
+                    tau=w["tau"], dt=dt, z_min=-1.0 + lo * dz, z_max=-1.0 + hi * dz,
+                    fields=fields)
+        _, mo = sodcase.run_oracle(case, steps)
+        for k in sodcase.PARITY_FIELDS:
+            got[k].append(mg[k][s0])
+            ref[k].append(mo[k][s0 - lo])
+    for k in sodcase.PARITY_FIELDS:
+        err = sodcase.rel_err(got[k], ref[k])
+        assert err <= tol, (k, err, samples)
+
+
+def test_checkpoint_resume_is_bitwise():
+    from paper_1612_01287_gb300 import Sod
+    case = sodcase.gpu_kwargs(small_case())
+    with Sod(precision="f32", **case) as a:
+        a.step(30)
+        ref = a.get_state()
+    with Sod(precision="f32", **case) as b:
+        b.step(12)
+        snap = b.get_state()
+    with Sod(precision="f32", **case) as c:
+        c.set_state(snap)
+        c.step(18)
+        got = c.get_state()
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_deterministic_repeat():
+    from paper_1612_01287_gb300 import Sod
+    case = sodcase.gpu_kwargs(small_case())
+    out = []
+    for _ in range(2):
+        with Sod(precision="f32", **case) as s:
+            s.step(20)
+            out.append(s.get_state())
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_nonphysical_state_reported():
+    """A negative density is caught on the device and reported on the host."""
+    from paper_1612_01287_gb300 import RslbError, Sod
+    Z = 32
+    n = np.ones(Z)
+    n[5] = -1.0
+    with pytest.raises(RslbError) as ei:
+        Sod(Z=Z, Q_xi=6, Q_L=2, bc="outflow", tau=1e-2, dt=1e-3,
+            fields=(n, np.ones(Z), np.zeros(Z)))
+    assert ei.value.code == 6
+    # a NaN planted in the populations is reported by the next sync
+    with Sod(Z=Z, Q_xi=6, Q_L=2, bc="outflow", tau=1e-2, dt=1e-3, precision="f64") as s:
+        f = s.get_state()
+        f[:, 7] = np.nan
+        s.set_state(f)
+        s.step(1)
+        with pytest.raises(RslbError) as ei:
+            s.sync()
+        assert ei.value.code == 6 and "cell" in str(ei.value)
