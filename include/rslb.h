@@ -114,6 +114,10 @@ typedef struct rslb_config {
   const double* n0;
   const double* T0;
   const double* beta0;
+  /* Cells per CTA tile of the stage kernel: 0 = automatic (largest tile that
+   * keeps two CTAs per SM); otherwise 32 or 16 (RSLB_F32), 16 or 8
+   * (RSLB_F64).  A tuning knob; results do not depend on it. */
+  int tile_cells;
 } rslb_config;
 
 typedef struct rslb_handle rslb_handle;

@@ -37,7 +37,8 @@ class Config(ctypes.Structure):
                 ("lambda_ref", ctypes.c_double), ("dt", ctypes.c_double),
                 ("nL", ctypes.c_double), ("TL", ctypes.c_double), ("betaL", ctypes.c_double),
                 ("nR", ctypes.c_double), ("TR", ctypes.c_double), ("betaR", ctypes.c_double),
-                ("n0", ctypes.c_void_p), ("T0", ctypes.c_void_p), ("beta0", ctypes.c_void_p)]
+                ("n0", ctypes.c_void_p), ("T0", ctypes.c_void_p), ("beta0", ctypes.c_void_p),
+                ("tile_cells", ctypes.c_int)]
 
 
 _lib = None
@@ -109,7 +110,8 @@ class Sod:
 
     def __init__(self, Z, Q_xi, Q_L=3, N_Omega=None, z_min=-1.0, z_max=1.0, precision="f32",
                  bc="outflow", tau_mode="const", tau=1e-3, tau_AW0=0.0, lambda_ref=1.0, dt=5e-4,
-                 left=(1.0, 1.0, 0.0), right=(0.125, 0.8, 0.0), fields=None, stream=None):
+                 left=(1.0, 1.0, 0.0), right=(0.125, 0.8, 0.0), fields=None, stream=None,
+                 tile_cells=0):
         """left/right: (n, T, beta); fields: optional (n0, T0, beta0) arrays of length Z."""
         if N_Omega is None:
             N_Omega = min(Q_xi - 1, 5)
@@ -124,7 +126,7 @@ class Sod:
                      F64 if self.fp64 else F32, BC[bc] if isinstance(bc, str) else int(bc),
                      TAU[tau_mode] if isinstance(tau_mode, str) else int(tau_mode),
                      tau, tau_AW0, lambda_ref, dt, left[0], left[1], left[2],
-                     right[0], right[1], right[2], None, None, None)
+                     right[0], right[1], right[2], None, None, None, int(tile_cells))
         if fields is not None:
             arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in fields]
             self._keep = arrs

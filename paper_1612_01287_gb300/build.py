@@ -43,7 +43,10 @@ def build(force=False, verbose=False, extra_flags=()):
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
         return LIB_PATH
     nvcc = _nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+    # host code: no floating-point contraction, so x86-64 and aarch64 builds
+    # give the same host-side numbers (quadrature nodes, cell centres)
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                     "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE,
                      "--expt-relaxed-constexpr"] + list(extra_flags)
     if verbose:
         common += ["-Xptxas", "-v"]

@@ -205,6 +205,8 @@ struct rslb_handle {
   void* t_gL;
   void* t_gR;
   int* t_kidx;
+  int* t_rowv;
+  int nneg;
   double* t_gl_t;
   double* t_gl_w;
   // FP64 tables
@@ -250,7 +252,7 @@ SodTablesF64 tables64_of(const rslb_handle* h) {
 void free_handle(rslb_handle* h) {
   if (!h) return;
   void* ptrs[] = {h->F[0], h->F[1], h->F[2], h->t_mw, h->t_xi, h->t_wp, h->t_L1k, h->t_gL,
-                  h->t_gR, h->t_kidx, h->t_gl_t, h->t_gl_w, h->d_xi, h->d_p, h->d_wp,
+                  h->t_gR, h->t_kidx, h->t_rowv, h->t_gl_t, h->t_gl_w, h->d_xi, h->d_p, h->d_wp,
                   h->d_L1k, h->d_err, h->d_fields};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -331,7 +333,16 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
   int max_smem = 0;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const bool fp64 = c.precision == RSLB_F64;
-  SodLaunch L = sod_pick_launch(fp64, V, QL, max_smem);
+  SodLaunch L = sod_pick_launch(fp64, V, QL, nm, max_smem);
+  if (c.tile_cells != 0) {
+    // explicit tile width (tuning): must be one the kernels are built for
+    const bool okB = fp64 ? (c.tile_cells == 16 || c.tile_cells == 8)
+                          : (c.tile_cells == 32 || c.tile_cells == 16);
+    if (!okB)
+      return set_error(RSLB_ERR_ARG, "rslb_init: tile_cells must be 0 or one of %s",
+                       fp64 ? "16, 8" : "32, 16");
+    L.B = c.tile_cells;
+  }
   if (L.B == 0)
     return set_error(RSLB_ERR_UNSUPPORTED, "rslb_init: V = %d velocities do not fit one tile", V);
 
@@ -379,6 +390,14 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
       for (int m = 0; m < nm; ++m) wp[(size_t)m * V + v] = wj[j] * wk[k] * legendre_p(m, x);
     }
   }
+  // rows ordered negative-xi first (ascending v within each group)
+  std::vector<int> rowv;
+  rowv.reserve(V);
+  for (int v = 0; v < V; ++v)
+    if (xiv[v] < 0.0) rowv.push_back(v);
+  h->nneg = (int)rowv.size();
+  for (int v = 0; v < V; ++v)
+    if (!(xiv[v] < 0.0)) rowv.push_back(v);
   std::vector<double> zeros(V, 0.0);
   int rc = RSLB_OK;
   auto up = [&](void** dst, const std::vector<double>& src) {
@@ -391,6 +410,7 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
   if (!rc) rc = up(&h->t_gL, zeros);
   if (!rc) rc = up(&h->t_gR, zeros);
   if (!rc) rc = upload_int(&h->t_kidx, kidx);
+  if (!rc) rc = upload_int(&h->t_rowv, rowv);
   if (!rc) rc = upload<double>((void**)&h->t_gl_t, glt);
   if (!rc) rc = upload<double>((void**)&h->t_gl_w, glw);
   if (!rc) rc = upload<double>((void**)&h->d_xi, xiv);
@@ -511,11 +531,14 @@ static cudaError_t enqueue_steps(rslb_handle* h, int nsteps) {
   T* F2 = (T*)h->F[2];
   for (int n = 0; n < nsteps; ++n) {
     cudaError_t e;
-    e = sod_stage_launch<T>(h->launch, h->geom, tb, F0, F0, F1, 0, h->d_err, h->stream);
+    e = sod_stage_launch<T>(h->launch, h->geom, tb, h->t_rowv, h->nneg, F0, F0, F1, 0, h->d_err,
+                            h->stream);
     if (e != cudaSuccess) return e;
-    e = sod_stage_launch<T>(h->launch, h->geom, tb, F1, F0, F2, 1, h->d_err, h->stream);
+    e = sod_stage_launch<T>(h->launch, h->geom, tb, h->t_rowv, h->nneg, F1, F0, F2, 1, h->d_err,
+                            h->stream);
     if (e != cudaSuccess) return e;
-    e = sod_stage_launch<T>(h->launch, h->geom, tb, F2, F0, F0, 2, h->d_err, h->stream);
+    e = sod_stage_launch<T>(h->launch, h->geom, tb, h->t_rowv, h->nneg, F2, F0, F0, 2, h->d_err,
+                            h->stream);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

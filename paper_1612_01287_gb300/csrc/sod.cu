@@ -2,44 +2,114 @@
 //
 // One CTA owns a tile of B consecutive cells and all V velocities.  A stage
 // (Eq. rk3) is one launch:
-//   1. the tile plus a 3-cell halo on each side is staged in shared memory
-//      (velocity-major rows, boundary cells mapped by the boundary condition);
-//   2. moments: each lane owns velocity rows, accumulates the five sums of the
-//      factored Landau form (Kahan-compensated in FP32), and a warp-shuffle
-//      tree reduces them across the velocity set;
-//   3. per cell: Landau matching in FP64 (Sec. II E), relaxation time, and the
-//      f^eq expansion coefficients (Sec. III D) by a Gauss-Legendre rule spread
-//      over all threads of the CTA and reduced by shuffles;
-//   4. per (velocity, cell): WENO5 flux difference (Sec. III F) along the row
-//      with a sliding register window, f^eq from the per-cell coefficients,
-//      Anderson-Witting relaxation (Eq. L_Sod) and the RK combination;
-//   5. coalesced store of the tile interior (plus the f_n term of stages 2, 3).
+//   1. the tile plus a 4-cell halo on each side is staged in shared memory
+//      with 16-byte cp.async copies (velocity-major rows; boundary tiles map
+//      out-of-domain cells through the boundary condition);
+//   2. moments: each warp owns a 16-byte column chunk of cells and its lanes
+//      own velocity rows; the five sums of the factored Landau form are
+//      accumulated in blocks of four rows and the blocks are added with Kahan
+//      compensation (FP32), then a warp-shuffle tree in FP64 reduces them
+//      across the velocity set;
+//   3. per cell: Landau matching in FP64 (Sec. II E), the relaxation time, and
+//      the f^eq expansion coefficients (Sec. III D) by a Gauss-Legendre rule
+//      spread over the CTA and reduced by shuffles;
+//   4. per (velocity, cell): the WENO5 flux difference (Sec. III F) along the
+//      row, written in terms of first and second differences of J = xi f so
+//      that a sliding window shares them between neighbouring faces; f^eq
+//      from the per-cell coefficients; Anderson-Witting relaxation
+//      (Eq. L_Sod); the RK combination.  Rows are visited negative-xi first so
+//      that the upwind direction is uniform within a warp;
+//   5. vectorised, coalesced store of the tile interior (with the f_n term of
+//      stages 2 and 3).
+// Shared-memory rows have a pitch whose 16-byte count is odd, so the 16-byte
+// accesses of eight consecutive rows fall in distinct bank groups.
 #include "rslb_device.cuh"
 #include "sod.cuh"
 
 namespace rslb {
 
-constexpr int kThreads = 256;
 constexpr int kMaxQL = 8;
+constexpr int kHalo = 4;
+constexpr int kMaxMP = 16;  // kMaxM rounded up to a whole number of 16-byte vectors
 
-template <typename T, int B>
-struct SodTile {
-  // row pitch of the staged tile: B + 6 cells, made odd so that lanes that
-  // own consecutive rows hit distinct shared-memory banks
-  static constexpr int W = B + 6;
-  static constexpr int P = (W % 2 == 0) ? W + 1 : W;
-  __host__ __device__ static size_t tile_bytes(int V) { return sizeof(T) * (size_t)V * P; }
-  __host__ __device__ static size_t extra_bytes() {
-    return sizeof(double) * (5 * B + 8 * B) + sizeof(T) * (kMaxQL * kMaxM * B + 2 * B);
-  }
-  __host__ __device__ static size_t smem_bytes(int V) {
-    size_t t = (tile_bytes(V) + 15) & ~size_t(15);
-    return t + extra_bytes();
+template <typename T> struct V16;
+template <> struct V16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <> struct V16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+template <typename T>
+__host__ __device__ constexpr int tile_pitch(int W) {
+  // smallest P >= W with P a multiple of the 16-byte vector and P/vector odd
+  constexpr int n = V16<T>::n;
+  int p = (W + n - 1) / n;
+  if (p % 2 == 0) ++p;
+  return p * n;
+}
+
+template <typename T>
+__host__ __device__ inline int coef_pitch(int nm) {
+  constexpr int n = V16<T>::n;
+  return (nm + n - 1) / n * n;
+}
+
+// Shared-memory carve-up of one CTA (all offsets 16-byte aligned).
+template <typename T>
+struct SodSmem {
+  size_t tile, outb, msum, cell, coef, gco, total;
+  __host__ __device__ SodSmem(int V, int B, int QL, int nm, bool seg) {
+    auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const int P = tile_pitch<T>(B + 2 * kHalo);
+    tile = 0;
+    outb = al(sizeof(T) * (size_t)V * P);
+    msum = outb + (seg ? al(sizeof(T) * (size_t)V * B) : 0);
+    cell = msum + al(sizeof(double) * 5 * B);
+    coef = cell + al(sizeof(double) * 8 * B);
+    gco = coef + al(sizeof(T) * (size_t)QL * B * coef_pitch<T>(nm));
+    total = gco + al(sizeof(T) * 2 * B);
   }
 };
 
 __device__ __forceinline__ void report_error(int* err, int code, int cell) {
   if (atomicCAS(err, 0, code) == 0) err[1] = cell;
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  return x;
+}
+
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::);
+}
+
+template <typename T>
+__device__ __forceinline__ T load_cell(const T* __restrict__ fin, const SodGeom& g,
+                                       const SodTables<T>& tb, int v, int s) {
+  if (s >= 0 && s < g.Z) return fin[(size_t)v * g.ldz + s];
+  if (g.bc == kBcPeriodic) {
+    int sp = s % g.Z;
+    if (sp < 0) sp += g.Z;
+    return fin[(size_t)v * g.ldz + sp];
+  }
+  if (g.bc == kBcOutflow) return fin[(size_t)v * g.ldz + (s < 0 ? 0 : g.Z - 1)];
+  return s < 0 ? tb.ghostL[v] : tb.ghostR[v];
 }
 
 // Kahan-compensated accumulation (FP32) / plain accumulation (FP64).
@@ -60,120 +130,234 @@ template <> struct Acc<double> {
   __device__ __forceinline__ double value() const { return s; }
 };
 
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-  return x;
-}
-
+// ---------------------------------------------------------------------------
+// WENO5 face correction in difference form.
+// For the upwind-ordered values (a, b, c, d, e) of Sec. III F with first
+// differences D0 = b-a, D1 = c-b, D2 = d-c, D3 = e-d and second differences
+// S1 = a-2b+c, S2 = b-2c+d, S3 = c-2d+e (K_q = 13/12 S_q^2):
+//   sigma_1 = K_1 + (3 D1 - D0)^2/4, sigma_2 = K_2 + (D1 + D2)^2/4,
+//   sigma_3 = K_3 + (D3 - 3 D2)^2/4,
+//   F^q = c + g_q/6 with g_1 = 5 D1 - 2 D0, g_2 = D1 + 2 D2, g_3 = 4 D2 - D3,
+// so F = c + (omega . g)/6.  With omega_q ~ delta_q / sigma_q^2 multiplied
+// through by prod_p (sigma_p/sigma_max)^2, the limiting rules (i)-(iii) of
+// the paper all reduce to "correction = 0" when every product vanishes (the
+// g_q of the vanishing stencils are exactly zero there), and rule (iii) is
+// the natural limit of the formula.  Returns (omega . g) (without the 1/6).
+// ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ T load_cell(const T* __restrict__ fin, const SodGeom& g,
-                                       const SodTables<T>& tb, int v, int s) {
-  if (s >= 0 && s < g.Z) return fin[(size_t)v * g.ldz + s];
-  if (g.bc == kBcPeriodic) {
-    int sp = s % g.Z;
-    if (sp < 0) sp += g.Z;
-    return fin[(size_t)v * g.ldz + sp];
-  }
-  if (g.bc == kBcOutflow) return fin[(size_t)v * g.ldz + (s < 0 ? 0 : g.Z - 1)];
-  return s < 0 ? tb.ghostL[v] : tb.ghostR[v];
+__device__ __forceinline__ T weno_corr(T D0, T D1, T D2, T D3, T K1, T K2, T K3) {
+  const T e1 = T(3) * D1 - D0, e2 = D1 + D2, e3 = D3 - T(3) * D2;
+  const T s1 = K1 + T(0.25) * e1 * e1;
+  const T s2 = K2 + T(0.25) * e2 * e2;
+  const T s3 = K3 + T(0.25) * e3 * e3;
+  const T g1 = T(5) * D1 - T(2) * D0, g2 = D1 + T(2) * D2, g3 = T(4) * D2 - D3;
+  // Values below the smallest normal number count as zero: the FP32 reciprocal
+  // flushes subnormal inputs, and a vanishing denominator means the
+  // correction vanishes (limit rules).
+  const T tiny = Prec<T>::tiny();
+  const T smax = fmax(s1, fmax(s2, s3));
+  const T inv = smax > tiny ? fast_rcp(smax) : T(0);
+  const T r1 = s1 * inv, r2 = s2 * inv, r3 = s3 * inv;
+  const T t1 = r1 * r1, t2 = r2 * r2, t3 = r3 * r3;
+  const T n1 = T(0.1) * (t2 * t3), n2 = T(0.6) * (t1 * t3), n3 = T(0.3) * (t1 * t2);
+  const T den = n1 + n2 + n3;
+  const T num = n1 * g1 + n2 * g2 + n3 * g3;
+  return den > tiny ? num * fast_rcp(den) : T(0);
 }
 
-// Phase 4 for one work unit: velocity row v, local cells [i0, i0 + SL).
-// If out != nullptr the results are kept in registers (segmented rows share
-// halo cells, so they may only be written back after a barrier); otherwise
-// they are written in place, which is safe because a row is owned by exactly
-// one thread and the window has already consumed the overwritten cell.
-template <typename T, int B, int SL>
-__device__ __forceinline__ void sweep_row(T* __restrict__ row, int v, int i0, const SodGeom& g,
-                                          const SodTables<T>& tb, const T* __restrict__ coef,
-                                          const T* __restrict__ gco, T* out) {
-  const T xi = tb.xi[v];
-  const int k = tb.kidx[v];
-  T wp[kMaxM];
+// 16-byte chunk of a shared-memory row as scalars.
+template <typename T>
+__device__ __forceinline__ void ld_chunk(const T* p, T* out) {
+  using VT = typename V16<T>::type;
+  const VT v = *reinterpret_cast<const VT*>(p);
+  if constexpr (V16<T>::n == 4) {
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  } else {
+    out[0] = v.x; out[1] = v.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st_chunk(T* p, const T* in) {
+  using VT = typename V16<T>::type;
+  VT v;
+  if constexpr (V16<T>::n == 4) {
+    v.x = in[0]; v.y = in[1]; v.z = in[2]; v.w = in[3];
+  } else {
+    v.x = in[0]; v.y = in[1];
+  }
+  *reinterpret_cast<VT*>(p) = v;
+}
+
+// ---------------------------------------------------------------------------
+// Phase 4: sweep one row segment [i0, i0+SL) (local cells; tile element
+// e = cell + kHalo) in chunks of VN cells with a sliding window of J = xi f
+// over cells [i-4, i+VN+4) of the current chunk start i.  POS: xi > 0.
+// Positive: face s+1/2 uses J_{s-2..s+2} with centre J_s:
+//   (D0..D3) = Delta_{s-2..s+1}, (K1, K2, K3) = K_{s-1}, K_s, K_{s+1}.
+// Negative: the mirror (J_{s+3}, ..., J_{s-1}) with centre J_{s+1}:
+//   (D0..D3) = -Delta_{s+2}, -Delta_{s+1}, -Delta_s, -Delta_{s-1},
+//   (K1, K2, K3) = K_{s+2}, K_{s+1}, K_s.
+// (Delta_s = J_{s+1} - J_s, K_s = 13/12 (J_{s-1} - 2 J_s + J_{s+1})^2.)
+// The flux difference of cell i is then
+//   POS: F_{i+1/2} - F_{i-1/2} = Delta_{i-1} + (C_{i+1/2} - C_{i-1/2})/6,
+//   NEG: F_{i+1/2} - F_{i-1/2} = Delta_i     + (C_{i+1/2} - C_{i-1/2})/6.
+// With the loop fully unrolled, differences shared between neighbouring
+// faces are computed once (common subexpressions across iterations).
+// ---------------------------------------------------------------------------
+template <typename T, bool POS>
+__device__ __forceinline__ T face_corr(const T* J, int wc) {
+  // J: window values, wc: window index of the face's left cell
+  const T k13 = T(13) / T(12);
+  auto D = [&](int c) { return J[c + 1] - J[c]; };
+  auto K = [&](int c) {
+    const T s2 = (J[c + 1] - J[c]) - (J[c] - J[c - 1]);
+    return k13 * s2 * s2;
+  };
+  if constexpr (POS)
+    return weno_corr<T>(D(wc - 2), D(wc - 1), D(wc), D(wc + 1), K(wc - 1), K(wc), K(wc + 1));
+  else
+    return weno_corr<T>(-D(wc + 2), -D(wc + 1), -D(wc), -D(wc - 1), K(wc + 2), K(wc + 1),
+                        K(wc));
+}
+
+template <typename T, bool POS, int SL>
+__device__ __forceinline__ void sweep_segment(const T* row, T* orow, int i0, T xi,
+                                              const T* __restrict__ wp, int nm, int MP,
+                                              const T* __restrict__ ck,
+                                              const T* __restrict__ gco, T inv_dz, T dt) {
+  constexpr int VN = V16<T>::n;
+  constexpr int NW = VN + 2 * kHalo;  // window cells [i-4, i+VN+4)
+  const T sixth = T(1) / T(6);
+  T R[NW];  // f at cells i-4+c
+  T J[NW];  // J = xi f at the same cells
 #pragma unroll
-  for (int m = 0; m < kMaxM; ++m) wp[m] = (m < g.nm) ? tb.wp[m * g.V + v] : T(0);
-  const bool pos = xi > T(0);
-  const T inv_dz = T(g.inv_dz), dt = T(g.dt);
-  const T* ck = coef + (size_t)k * kMaxM * B;
-  // window J[0..6] = J at local cells i-3 .. i+3 (tile element e = cell + 3)
-  T J0 = xi * row[i0 + 0], J1 = xi * row[i0 + 1], J2 = xi * row[i0 + 2];
-  T J3 = xi * row[i0 + 3], J4 = xi * row[i0 + 4], J5 = xi * row[i0 + 5];
-  T J6 = xi * row[i0 + 6];
-  // left face of cell i0
-  T Fl = weno5_face<T>(pos ? J0 : J5, pos ? J1 : J4, pos ? J2 : J3, pos ? J3 : J2,
-                       pos ? J4 : J1);
+  for (int c = 0; c < NW; c += VN) ld_chunk<T>(row + i0 + c, R + c);
 #pragma unroll
-  for (int ii = 0; ii < SL; ++ii) {
-    const int i = i0 + ii;
-    const T Fr = weno5_face<T>(pos ? J1 : J6, pos ? J2 : J5, pos ? J3 : J4, pos ? J4 : J3,
-                               pos ? J5 : J2);
-    const T f = row[i + 3];
-    T feq = T(0);
+  for (int c = 0; c < NW; ++c) J[c] = xi * R[c];
+  // correction at the left face of cell i0 (window cell of its left cell: 3)
+  T Cl = face_corr<T, POS>(J, kHalo - 1);
 #pragma unroll
-    for (int m = 0; m < kMaxM; ++m)
-      if (m < g.nm) feq += ck[m * B + i] * wp[m];
-    const T coll = (gco[i] - gco[B + i] * xi) * (f - feq);
-    const T L = -(Fr - Fl) * inv_dz - coll;
-    const T r = f + dt * L;
-    if (out) out[ii] = r; else row[i + 3] = r;
-    Fl = Fr;
-    if (ii + 1 < SL) {
-      J0 = J1; J1 = J2; J2 = J3; J3 = J4; J4 = J5; J5 = J6;
-      J6 = xi * row[i + 7];
+  for (int t = 0; t < SL / VN; ++t) {
+    const int i = i0 + t * VN;
+    T out[VN];
+#pragma unroll
+    for (int c = 0; c < VN; ++c) {
+      const int wc = kHalo + c;  // window index of cell i + c
+      const T Cr = face_corr<T, POS>(J, wc);
+      const T dF = (POS ? (J[wc] - J[wc - 1]) : (J[wc + 1] - J[wc])) + (Cr - Cl) * sixth;
+      Cl = Cr;
+      const T* cc = ck + (size_t)(i + c) * MP;
+      T feq = T(0);
+#pragma unroll
+      for (int m0 = 0; m0 < kMaxMP; m0 += VN) {
+        if (m0 < nm) {
+          T cv[VN];
+          ld_chunk<T>(cc + m0, cv);
+#pragma unroll
+          for (int q = 0; q < VN; ++q) feq += cv[q] * wp[m0 + q];
+        }
+      }
+      const T f = R[kHalo + c];
+      const T coll = (gco[2 * (i + c)] - gco[2 * (i + c) + 1] * xi) * (f - feq);
+      const T L = -dF * inv_dz - coll;
+      out[c] = f + dt * L;
     }
+    if (t + 1 < SL / VN) {
+      // slide the window by one chunk: load the chunk at cells i+VN+4 ..
+#pragma unroll
+      for (int c = 0; c < NW - VN; ++c) {
+        J[c] = J[c + VN];
+        R[c] = R[c + VN];
+      }
+      ld_chunk<T>(row + i + NW, R + NW - VN);  // tile element of cell i+VN+4 is i + NW
+#pragma unroll
+      for (int c = 0; c < VN; ++c) J[NW - VN + c] = xi * R[NW - VN + c];
+    }
+    st_chunk<T>(orow + kHalo + i, out);
   }
 }
 
-template <typename T, int B>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, int B, int NT>
+__global__ void __launch_bounds__(NT, 2)
 sod_stage_kernel(const T* __restrict__ fin, const T* __restrict__ fn, T* fout, int stage,
-                 int* err, SodGeom g, SodTables<T> tb, int nseg) {
-  using Tile = SodTile<T, B>;
-  constexpr int W = Tile::W, P = Tile::P;
+                 int* err, SodGeom g, SodTables<T> tb, const int* __restrict__ rowv, int nneg,
+                 int nseg) {
+  constexpr int VN = V16<T>::n;
+  constexpr int W = B + 2 * kHalo;
+  constexpr int P = tile_pitch<T>(W);
+  constexpr int CH = B / VN;  // 16-byte chunks of interior cells
+  static_assert(CH <= NT / 32, "one warp per interior chunk in the moment phase");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tile = reinterpret_cast<T*>(smem_raw);
-  double* msum = reinterpret_cast<double*>(smem_raw + ((Tile::tile_bytes(g.V) + 15) & ~size_t(15)));
-  double* cell = msum + 5 * B;
-  T* coef = reinterpret_cast<T*>(cell + 8 * B);
-  T* gco = coef + kMaxQL * kMaxM * B;
+  const int V = g.V;
+  const SodSmem<T> lay(V, B, g.QL, g.nm, nseg > 1);
+  T* tile = reinterpret_cast<T*>(smem_raw + lay.tile);
+  T* outb = (nseg > 1) ? reinterpret_cast<T*>(smem_raw + lay.outb) : nullptr;
+  double* msum = reinterpret_cast<double*>(smem_raw + lay.msum);
+  double* cell = reinterpret_cast<double*>(smem_raw + lay.cell);
+  T* coef = reinterpret_cast<T*>(smem_raw + lay.coef);
+  T* gco = reinterpret_cast<T*>(smem_raw + lay.gco);
+  const int MP = coef_pitch<T>(g.nm);
 
   const int s0 = blockIdx.x * B;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int V = g.V;
 
   // ---- 1. stage tile + halo ----
-  for (int idx = tid; idx < V * W; idx += kThreads) {
-    const int v = idx / W, e = idx - v * W;
-    tile[v * P + e] = load_cell<T>(fin, g, tb, v, s0 - 3 + e);
+  const bool interior = (s0 - kHalo >= 0) && (s0 + B + kHalo <= g.Z);
+  if (interior) {
+    constexpr int CPR = W / VN;  // chunks per row
+    for (int idx = tid; idx < V * CPR; idx += NT) {
+      const int v = idx / CPR, c = idx - v * CPR;
+      cp_async16(tile + v * P + c * VN, fin + (size_t)v * g.ldz + (s0 - kHalo) + c * VN);
+    }
+    cp_async_wait_all();
+  } else {
+    for (int idx = tid; idx < V * W; idx += NT) {
+      const int v = idx / W, e = idx - v * W;
+      tile[v * P + e] = load_cell<T>(fin, g, tb, v, s0 - kHalo + e);
+    }
   }
   __syncthreads();
 
   const bool collide = g.tau_mode != kTauNone;
   if (collide) {
-    // ---- 2. moments: lanes own rows, warps own cells ----
-    constexpr int CPW = B / (kThreads / 32);
-    Acc<T> acc[CPW][5];
-    for (int v = lane; v < V; v += 32) {
-      T w[5];
+    // ---- 2. moments: warp = 16-byte chunk of cells, lanes = rows ----
+    if (warp < CH) {
+      Acc<T> acc[VN][5];
+      for (int v0 = lane; v0 < V; v0 += 128) {
+        T blk[VN][5];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) w[q] = tb.mw[q * V + v];
-      const T* row = tile + v * P + 3 + warp * CPW;
+        for (int c = 0; c < VN; ++c)
 #pragma unroll
-      for (int c = 0; c < CPW; ++c) {
-        const T x = row[c];
+          for (int q = 0; q < 5; ++q) blk[c][q] = T(0);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) acc[c][q].add(x * w[q]);
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + 32 * u;
+          if (v < V) {
+            T x[VN];
+            ld_chunk<T>(tile + v * P + kHalo + warp * VN, x);
+            T w[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) w[q] = tb.mw[q * V + v];
+#pragma unroll
+            for (int c = 0; c < VN; ++c)
+#pragma unroll
+              for (int q = 0; q < 5; ++q) blk[c][q] += x[c] * w[q];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < VN; ++c)
+#pragma unroll
+          for (int q = 0; q < 5; ++q) acc[c][q].add(blk[c][q]);
       }
+#pragma unroll
+      for (int c = 0; c < VN; ++c)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const double s = warp_sum(acc[c][q].value());
+          if (lane == 0) msum[q * B + warp * VN + c] = s;
+        }
     }
-#pragma unroll
-    for (int c = 0; c < CPW; ++c)
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const double s = warp_sum(acc[c][q].value());
-        if (lane == 0) msum[q * B + warp * CPW + c] = s;
-      }
     __syncthreads();
 
     // ---- 3a. Landau matching and relaxation time, one thread per cell ----
@@ -203,166 +387,204 @@ sod_stage_kernel(const T* __restrict__ fin, const T* __restrict__ fn, T* fout, i
       cell[5 * B + c] = 2.0 * sh * sh;
       cell[6 * B + c] = (Lo.beta < 0.0) ? -1.0 : 1.0;
       cell[7 * B + c] = Lo.ok ? 1.0 : 0.0;
-      gco[c] = T(g0);
-      gco[B + c] = T(g1);
+      gco[2 * c] = T(g0);
+      gco[2 * c + 1] = T(g1);
     }
     __syncthreads();
 
     // ---- 3b. f^eq coefficients: G threads per cell share the nodes ----
     {
-      constexpr int G = kThreads / B;
+      constexpr int G = (256 / B) < 32 ? (256 / B) : 32;
       const int c = tid / G, q = tid - c * G;
-      const double ud = cell[2 * B + c];
-      const T A = T(cell[3 * B + c]), sh2 = T(cell[5 * B + c]);
-      const T uinv = (ud > 0.0) ? T(1.0 / ud) : T(0);
-      const bool at_rest = !(ud > 0.0);
-      T J3[kMaxM], J4[kMaxM];
+      if (c < B) {
+        const double ud = cell[2 * B + c];
+        const T A = T(cell[3 * B + c]), sh2 = T(cell[5 * B + c]);
+        const T uinv = (ud > 0.0) ? T(1.0 / ud) : T(0);
+        const bool at_rest = !(ud > 0.0);
+        T J3[kMaxM], J4[kMaxM];
 #pragma unroll
-      for (int m = 0; m < kMaxM; ++m) { J3[m] = T(0); J4[m] = T(0); }
-      for (int i = q; i < kAeqNodes; i += G)
-        aeq_node<T>(T(tb.gl_t[i]), T(tb.gl_w[i]), A, sh2, uinv, at_rest, g.nm, J3, J4);
+        for (int m = 0; m < kMaxM; ++m) { J3[m] = T(0); J4[m] = T(0); }
+        for (int i = q; i < kAeqNodes; i += G)
+          aeq_node<T>(T(tb.gl_t[i]), T(tb.gl_w[i]), A, sh2, uinv, at_rest, g.nm, J3, J4);
 #pragma unroll
-      for (int off = G / 2; off >= 1; off >>= 1)
+        for (int off = G / 2; off >= 1; off >>= 1)
 #pragma unroll
-        for (int m = 0; m < kMaxM; ++m)
-          if (m < g.nm) {
-            J3[m] += __shfl_xor_sync(0xffffffffu, J3[m], off);
-            J4[m] += __shfl_xor_sync(0xffffffffu, J4[m], off);
+          for (int m = 0; m < kMaxM; ++m)
+            if (m < g.nm) {
+              J3[m] += __shfl_xor_sync(0xffffffffu, J3[m], off, G);
+              J4[m] += __shfl_xor_sync(0xffffffffu, J4[m], off, G);
+            }
+        if (q == 0) {
+          // c''_{k,m} = sgn^m (2m+1)/2 (n r/4) [J3_m + (3 - x_k)(J3_m - theta J4_m)]
+          const double ok = cell[7 * B + c];
+          const T fac = T(ok * cell[0 * B + c] * cell[4 * B + c] * 0.25);
+          const T theta = T(cell[1 * B + c]);
+          const T sgn = T(cell[6 * B + c]);
+          T sm = fac;
+#pragma unroll
+          for (int m = 0; m < kMaxM; ++m) {
+            if (m < g.nm) {
+              const T h = sm * T(0.5 * (2 * m + 1));
+              const T d = J3[m] - theta * J4[m];
+              for (int k = 0; k < g.QL; ++k)
+                coef[((size_t)k * B + c) * MP + m] = h * (J3[m] + tb.L1k[k] * d);
+              sm *= sgn;
+            }
           }
-      if (q == 0) {
-        // c''_{k,m} = sgn^m (2m+1)/2 (n r/4) [J3_m + (3 - x_k)(J3_m - theta J4_m)]
-        const double ok = cell[7 * B + c];
-        const T fac = T(ok * cell[0 * B + c] * cell[4 * B + c] * 0.25);
-        const T theta = T(cell[1 * B + c]);
-        const T sgn = T(cell[6 * B + c]);
-        T sm = fac;
-#pragma unroll
-        for (int m = 0; m < kMaxM; ++m) {
-          if (m < g.nm) {
-            const T h = sm * T(0.5 * (2 * m + 1));
-            const T d = J3[m] - theta * J4[m];
-            for (int k = 0; k < g.QL; ++k)
-              coef[(k * kMaxM + m) * B + c] = h * (J3[m] + tb.L1k[k] * d);
-            sm *= sgn;
-          }
+          for (int m = g.nm; m < MP; ++m)
+            for (int k = 0; k < g.QL; ++k) coef[((size_t)k * B + c) * MP + m] = T(0);
         }
       }
     }
     __syncthreads();
   } else {
-    if (tid < B) { gco[tid] = T(0); gco[B + tid] = T(0); }
-    for (int i = tid; i < kMaxQL * kMaxM * B; i += kThreads) coef[i] = T(0);
+    for (int i = tid; i < 2 * B; i += NT) gco[i] = T(0);
+    for (int i = tid; i < g.QL * B * MP; i += NT) coef[i] = T(0);
     __syncthreads();
   }
 
   // ---- 4. WENO5 + relaxation + RK update, row sweeps ----
-  if (nseg == 1) {
-    for (int v = tid; v < V; v += kThreads)
-      sweep_row<T, B, B>(tile + v * P, v, 0, g, tb, coef, gco, nullptr);
-  } else if (nseg == 2) {
-    T out[B / 2];
-    const int v = tid % V, seg = tid / V;
-    const bool active = tid < 2 * V;
-    if (active) sweep_row<T, B, B / 2>(tile + v * P, v, seg * (B / 2), g, tb, coef, gco, out);
-    __syncthreads();
-    if (active)
+  const T inv_dz = T(g.inv_dz), dt = T(g.dt);
+  const int SLr = B / nseg;
+  for (int u = tid; u < V * nseg; u += NT) {
+    const int ir = u % V, seg = u / V;
+    const int v = rowv[ir];
+    const bool pos = ir >= nneg;
+    const T xi = tb.xi[v];
+    const int k = tb.kidx[v];
+    T wp[kMaxMP];
 #pragma unroll
-      for (int ii = 0; ii < B / 2; ++ii) tile[v * P + 3 + seg * (B / 2) + ii] = out[ii];
-  } else if (nseg == 4) {
-    T out[B / 4];
-    const int v = tid % V, seg = tid / V;
-    const bool active = tid < 4 * V;
-    if (active) sweep_row<T, B, B / 4>(tile + v * P, v, seg * (B / 4), g, tb, coef, gco, out);
-    __syncthreads();
-    if (active)
-#pragma unroll
-      for (int ii = 0; ii < B / 4; ++ii) tile[v * P + 3 + seg * (B / 4) + ii] = out[ii];
-  } else {
-    T out[B / 8];
-    const int v = tid % V, seg = tid / V;
-    const bool active = tid < 8 * V;
-    if (active) sweep_row<T, B, B / 8>(tile + v * P, v, seg * (B / 8), g, tb, coef, gco, out);
-    __syncthreads();
-    if (active)
-#pragma unroll
-      for (int ii = 0; ii < B / 8; ++ii) tile[v * P + 3 + seg * (B / 8) + ii] = out[ii];
+    for (int m = 0; m < kMaxMP; ++m) wp[m] = (m < g.nm) ? tb.wp[m * V + v] : T(0);
+    const T* row = tile + v * P;
+    T* orow = (nseg > 1) ? (outb + v * B - kHalo) : (tile + v * P);
+    const T* ck = coef + (size_t)k * B * MP;
+    const int i0 = seg * SLr;
+    // the segment length is one of B, B/2, B/4, B/8 (>= one 16-byte chunk)
+    if (SLr == B) {
+      if (pos) sweep_segment<T, true, B>(row, orow, i0, xi, wp, g.nm, MP, ck, gco, inv_dz, dt);
+      else sweep_segment<T, false, B>(row, orow, i0, xi, wp, g.nm, MP, ck, gco, inv_dz, dt);
+    } else if (SLr == B / 2) {
+      if (pos) sweep_segment<T, true, B / 2>(row, orow, i0, xi, wp, g.nm, MP, ck, gco, inv_dz, dt);
+      else sweep_segment<T, false, B / 2>(row, orow, i0, xi, wp, g.nm, MP, ck, gco, inv_dz, dt);
+    } else if constexpr (B / 4 >= VN) {
+      if (SLr == B / 4) {
+        if (pos) sweep_segment<T, true, B / 4>(row, orow, i0, xi, wp, g.nm, MP, ck, gco, inv_dz, dt);
+        else sweep_segment<T, false, B / 4>(row, orow, i0, xi, wp, g.nm, MP, ck, gco, inv_dz, dt);
+      } else if constexpr (B / 8 >= VN) {
+        if (pos) sweep_segment<T, true, B / 8>(row, orow, i0, xi, wp, g.nm, MP, ck, gco, inv_dz, dt);
+        else sweep_segment<T, false, B / 8>(row, orow, i0, xi, wp, g.nm, MP, ck, gco, inv_dz, dt);
+      }
+    }
   }
   __syncthreads();
 
-  // ---- 5. coalesced store ----
+  // ---- 5. coalesced store of the interior ----
   const T a = (stage == 1) ? T(0.75) : T(1.0 / 3.0);
   const T b = (stage == 1) ? T(0.25) : T(2.0 / 3.0);
-  for (int idx = tid; idx < V * B; idx += kThreads) {
-    const int v = idx / B, i = idx - v * B;
-    const int s = s0 + i;
-    if (s < g.Z) {
-      const size_t o = (size_t)v * g.ldz + s;
-      T r = tile[v * P + 3 + i];
-      if (stage != 0) r = a * fn[o] + b * r;
-      fout[o] = r;
+  const T* res = (nseg > 1) ? outb : tile + kHalo;
+  const int rp = (nseg > 1) ? B : P;
+  if (s0 + B <= g.Z) {
+    for (int idx = tid; idx < V * CH; idx += NT) {
+      const int v = idx / CH, c = idx - v * CH;
+      const size_t o = (size_t)v * g.ldz + s0 + c * VN;
+      T r[VN];
+      ld_chunk<T>(res + v * rp + c * VN, r);
+      if (stage != 0) {
+        T fo[VN];
+        ld_chunk<T>(fn + o, fo);
+#pragma unroll
+        for (int q = 0; q < VN; ++q) r[q] = a * fo[q] + b * r[q];
+      }
+      st_chunk<T>(fout + o, r);
+    }
+  } else {
+    for (int idx = tid; idx < V * B; idx += NT) {
+      const int v = idx / B, i = idx - v * B;
+      const int s = s0 + i;
+      if (s < g.Z) {
+        const size_t o = (size_t)v * g.ldz + s;
+        T r = res[v * rp + i];
+        if (stage != 0) r = a * fn[o] + b * r;
+        fout[o] = r;
+      }
     }
   }
 }
 
-SodLaunch sod_pick_launch(bool fp64, int V, int QL, int max_smem) {
+template <typename T, int B, int NT>
+static size_t smem_for(int V, int QL, int nm, int nseg) {
+  return SodSmem<T>(V, B, QL, nm, nseg > 1).total;
+}
+
+static int pick_nseg(int V, int B, int NT, int VN) {
+  int nseg = 1;
+  while (nseg < 8 && B / (2 * nseg) >= VN && V * 2 * nseg <= NT) nseg *= 2;
+  return nseg;
+}
+
+SodLaunch sod_pick_launch(bool fp64, int V, int QL, int nm, int max_smem) {
   SodLaunch L{0, 0};
-  if (QL > kMaxQL || V < 1) return L;
-  const size_t half = (size_t)max_smem / 2 - 1024;
+  if (QL > kMaxQL || V < 1 || nm < 1 || nm > kMaxM) return L;
+  const size_t half = (size_t)max_smem / 2 - 2048;
   if (!fp64) {
-    if (SodTile<float, 32>::smem_bytes(V) <= half) return {32, SodTile<float, 32>::smem_bytes(V)};
-    if (SodTile<float, 16>::smem_bytes(V) <= (size_t)max_smem)
-      return {16, SodTile<float, 16>::smem_bytes(V)};
-    if (SodTile<float, 8>::smem_bytes(V) <= (size_t)max_smem)
-      return {8, SodTile<float, 8>::smem_bytes(V)};
+    const int n32 = pick_nseg(V, 32, 320, 4), n16 = pick_nseg(V, 16, 320, 4);
+    if (smem_for<float, 32, 320>(V, QL, nm, n32) <= half) return {32, 0};
+    if (smem_for<float, 16, 320>(V, QL, nm, n16) <= half) return {16, 0};
+    if (smem_for<float, 16, 320>(V, QL, nm, n16) <= (size_t)max_smem) return {16, 0};
   } else {
-    if (SodTile<double, 16>::smem_bytes(V) <= half) return {16, SodTile<double, 16>::smem_bytes(V)};
-    if (SodTile<double, 8>::smem_bytes(V) <= (size_t)max_smem)
-      return {8, SodTile<double, 8>::smem_bytes(V)};
+    const int n16 = pick_nseg(V, 16, 320, 2), n8 = pick_nseg(V, 8, 320, 2);
+    if (smem_for<double, 16, 320>(V, QL, nm, n16) <= half) return {16, 0};
+    if (smem_for<double, 8, 320>(V, QL, nm, n8) <= half) return {8, 0};
+    if (smem_for<double, 8, 320>(V, QL, nm, n8) <= (size_t)max_smem) return {8, 0};
   }
   return L;
 }
 
-static int pick_nseg(int V, int B) {
-  int nseg = 1;
-  while (nseg < 8 && B / (2 * nseg) >= 2 && V * 2 * nseg <= kThreads) nseg *= 2;
-  return nseg;
-}
-
 template <typename T, int B>
-static cudaError_t launch_b(const SodLaunch& L, const SodGeom& g, const SodTables<T>& tb,
+static cudaError_t launch_b(const SodGeom& g, const SodTables<T>& tb, const int* rowv, int nneg,
                             const T* fin, const T* fn, T* fout, int stage, int* err,
                             cudaStream_t st) {
-  static bool attr_set = false;  // per device this is cheap to repeat; keep it simple
+  constexpr int NT = 320;
+  static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sod_stage_kernel<T, B>,
+    cudaError_t e = cudaFuncSetAttribute(sod_stage_kernel<T, B, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  const int nseg = pick_nseg(g.V, B, NT, V16<T>::n);
+  const size_t smem = smem_for<T, B, NT>(g.V, g.QL, g.nm, nseg);
   const int grid = (g.Z + B - 1) / B;
-  sod_stage_kernel<T, B><<<grid, kThreads, L.smem, st>>>(fin, fn, fout, stage, err, g, tb,
-                                                         pick_nseg(g.V, B));
+  sod_stage_kernel<T, B, NT><<<grid, NT, smem, st>>>(fin, fn, fout, stage, err, g, tb, rowv,
+                                                     nneg, nseg);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t sod_stage_launch(const SodLaunch& L, const SodGeom& g, const SodTables<T>& tb,
-                             const T* fin, const T* fn, T* fout, int stage, int* err,
-                             cudaStream_t st) {
+                             const int* rowv, int nneg, const T* fin, const T* fn, T* fout,
+                             int stage, int* err, cudaStream_t st) {
   switch (L.B) {
-    case 32: return launch_b<T, 32>(L, g, tb, fin, fn, fout, stage, err, st);
-    case 16: return launch_b<T, 16>(L, g, tb, fin, fn, fout, stage, err, st);
-    case 8: return launch_b<T, 8>(L, g, tb, fin, fn, fout, stage, err, st);
-    default: return cudaErrorInvalidValue;
+    case 32:
+      if constexpr (sizeof(T) == 4) return launch_b<T, 32>(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
+      break;
+    case 16: return launch_b<T, 16>(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
+    case 8:
+      if constexpr (sizeof(T) == 8) return launch_b<T, 8>(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
+      break;
+    default: break;
   }
+  return cudaErrorInvalidValue;
 }
 
 template cudaError_t sod_stage_launch<float>(const SodLaunch&, const SodGeom&,
-                                             const SodTables<float>&, const float*, const float*,
-                                             float*, int, int*, cudaStream_t);
+                                             const SodTables<float>&, const int*, int,
+                                             const float*, const float*, float*, int, int*,
+                                             cudaStream_t);
 template cudaError_t sod_stage_launch<double>(const SodLaunch&, const SodGeom&,
-                                              const SodTables<double>&, const double*,
-                                              const double*, double*, int, int*, cudaStream_t);
+                                              const SodTables<double>&, const int*, int,
+                                              const double*, const double*, double*, int, int*,
+                                              cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Initialisation: per-cell FP64 coefficients, then populations.
@@ -373,9 +595,10 @@ __global__ void sod_init_coef_kernel(SodGeom g, SodTablesF64 tb, const double* _
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.Z) return;
   const double nn = n[s], TT = Tt[s], bb = beta[s];
+  double* cs = coef + (size_t)s * kMaxQL * kMaxM;
   if (!(nn > 0.0) || !(TT > 0.0) || !(fabs(bb) < 1.0)) {
     report_error(err, 6, s);
-    for (int i = 0; i < kMaxQL * kMaxM; ++i) coef[(size_t)s * kMaxQL * kMaxM + i] = 0.0;
+    for (int i = 0; i < kMaxQL * kMaxM; ++i) cs[i] = 0.0;
     return;
   }
   const double gam = 1.0 / sqrt((1.0 - bb) * (1.0 + bb));
@@ -385,18 +608,21 @@ __global__ void sod_init_coef_kernel(SodGeom g, SodTablesF64 tb, const double* _
   const double sh2 = 2.0 * sh * sh;
   const double uinv = u > 0.0 ? 1.0 / u : 0.0;
   double J3[kMaxM], J4[kMaxM];
+#pragma unroll
   for (int m = 0; m < kMaxM; ++m) { J3[m] = 0.0; J4[m] = 0.0; }
   for (int i = 0; i < kAeqNodes; ++i)
     aeq_node<double>(tb.gl_t[i], tb.gl_w[i], A, sh2, uinv, !(u > 0.0), g.nm, J3, J4);
   const double r = u > 0.0 ? A / u : 1.0;
   double sm = nn * r * 0.25;
   const double sgn = bb < 0.0 ? -1.0 : 1.0;
-  for (int m = 0; m < g.nm; ++m) {
-    const double h = sm * 0.5 * (2 * m + 1);
-    const double d = J3[m] - TT * J4[m];
-    for (int k = 0; k < g.QL; ++k)
-      coef[(size_t)s * kMaxQL * kMaxM + k * kMaxM + m] = h * (J3[m] + tb.L1k[k] * d);
-    sm *= sgn;
+#pragma unroll
+  for (int m = 0; m < kMaxM; ++m) {
+    if (m < g.nm) {
+      const double h = sm * 0.5 * (2 * m + 1);
+      const double d = J3[m] - TT * J4[m];
+      for (int k = 0; k < g.QL; ++k) cs[k * kMaxM + m] = h * (J3[m] + tb.L1k[k] * d);
+      sm *= sgn;
+    }
   }
 }
 
@@ -444,6 +670,7 @@ __global__ void sod_moments_kernel(SodGeom g, SodTablesF64 tb, const T* __restri
   const int lane = threadIdx.x & 31;
   if (s >= g.Z) return;
   double S[10];
+#pragma unroll
   for (int q = 0; q < 10; ++q) S[q] = 0.0;
   for (int v = lane; v < g.V; v += 32) {
     const double x = (double)f[(size_t)v * g.ldz + s];
@@ -459,6 +686,7 @@ __global__ void sod_moments_kernel(SodGeom g, SodTablesF64 tb, const T* __restri
     S[8] += x * p * (1.0 - xi) * (1.0 - xi);
     S[9] += x * p * (1.0 - xi) * (1.0 + xi);
   }
+#pragma unroll
   for (int q = 0; q < 10; ++q) S[q] = warp_sum(S[q]);
   if (lane != 0) return;
   const LandauOut L = landau_factored(S[5], S[6], S[7], S[8], S[9]);

@@ -51,13 +51,15 @@ struct SodLaunch {
 };
 
 // Pick the tile width for V velocities; returns B = 0 if V does not fit.
-SodLaunch sod_pick_launch(bool fp64, int V, int QL, int max_smem);
+SodLaunch sod_pick_launch(bool fp64, int V, int QL, int nm, int max_smem);
 
 // Enqueue one RK stage (stage = 0, 1, 2): fout = stage update of fin (and fn).
+// rowv: velocity rows ordered with negative xi first (nneg of them), so that
+// the upwind direction is uniform within a warp.
 template <typename T>
 cudaError_t sod_stage_launch(const SodLaunch& L, const SodGeom& g, const SodTables<T>& tb,
-                             const T* fin, const T* fn, T* fout, int stage, int* err,
-                             cudaStream_t st);
+                             const int* rowv, int nneg, const T* fin, const T* fn, T* fout,
+                             int stage, int* err, cudaStream_t st);
 
 // Per-cell coefficients c''_{k,m} (FP64) of f^eq for given (n, T, beta) per
 // cell, then populations f[v*ldz + s] = sum_m c''_{k(v),m}(s) wp_m(v).

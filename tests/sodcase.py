@@ -43,7 +43,7 @@ def run_gpu(case, steps, precision):
 
 
 def rel_err(a, b):
-    """max_s |a - b| / max_s |b| (normalised by the field's maximum)."""
+    """max_s |a - b| / max_s |b| (normalised by the reference field's maximum)."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     scale = np.abs(b).max()
@@ -52,14 +52,48 @@ def rel_err(a, b):
     return np.abs(a - b).max() / scale
 
 
+def field_errors(mg, mo):
+    """Parity metric on n, E, beta, Pi.
+
+    n and E: max-normalised relative error.  beta: absolute error (beta is a
+    velocity in units of c, and vanishes in the unperturbed chambers).  Pi: error
+    normalised by the pressure scale max_s P (Pi is a small difference of O(P)
+    stresses, Eq. pi_val, so its own maximum is not a meaningful scale)."""
+    e = {"n": rel_err(mg["n"], mo["n"]), "E": rel_err(mg["E"], mo["E"]),
+         "beta": float(np.abs(np.asarray(mg["beta"]) - np.asarray(mo["beta"])).max())}
+    e["Pi"] = float(np.abs(np.asarray(mg["Pi"]) - np.asarray(mo["Pi"])).max() / np.abs(mo["P"]).max())
+    return e
+
+
 def compare(case, steps, precision, tol_fields, tol_pop=None):
     """Run both sides; return dict of errors; assert against the tolerances."""
     fg, mg = run_gpu(case, steps, precision)
     fo, mo = run_oracle(case, steps)
-    errs = {k: rel_err(mg[k], mo[k]) for k in PARITY_FIELDS}
+    errs = field_errors(mg, mo)
     errs["populations"] = rel_err(fg, fo.T)
     for k in PARITY_FIELDS:
         assert errs[k] <= tol_fields, (k, errs)
     if tol_pop is not None:
         assert errs["populations"] <= tol_pop, errs
     return errs
+
+
+def oracle_rounding_envelope(case, steps, every=16, seed=3):
+    """How far the oracle itself moves when its state is nudged by one ulp (random
+    sign, every `every` steps): the size of differences that rounding alone
+    produces in this nonlinear scheme over `steps` steps."""
+    p = oracle_params(case)
+    f = oracle.sod_init_fields(p, *case["fields"]) if "fields" in case else oracle.sod_init_riemann(p)
+    rng = np.random.default_rng(seed)
+    g = f.copy()
+    done = 0
+    while done < steps:
+        n = min(every, steps - done)
+        f = oracle.sod_steps(p, f, n)
+        g = np.nextafter(g, np.where(rng.random(g.shape) < 0.5, -np.inf, np.inf))
+        g = oracle.sod_steps(p, g, n)
+        done += n
+    mf, mg = oracle.sod_moments(p, f), oracle.sod_moments(p, g)
+    e = field_errors(mg, mf)
+    e["populations"] = rel_err(g, f)
+    return e
