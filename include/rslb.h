@@ -174,6 +174,44 @@ int rslb_set_state(rslb_handle* h, const void* f, int on_device);
 /* Simulation time and step count of the handle (host-side bookkeeping). */
 int rslb_time(const rslb_handle* h, double* t, long long* steps);
 
+/*
+ * Allocation-free shock-tube step (no counterpart in the paper; a service for
+ * callers that cannot allocate device memory).
+ *
+ * Some callers may not call cudaMalloc or any allocating routine: code that runs
+ * while another component owns all device memory (a framework's caching
+ * allocator, a fixed memory budget), plugins loaded into a host that forbids
+ * allocation in its compute callbacks, or real-time loops where an allocation's
+ * implicit device synchronisation is not acceptable.  This entry point does
+ * the same work as rslb_init + rslb_step without allocating anything: the RK
+ * stage buffers, velocity tables and error word live in one static device
+ * array of RSLB_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the
+ * library holds until the process exits.
+ *
+ *   cfg:    the configuration, as for rslb_init (n0/T0/beta0 and tile_cells
+ *           are ignored; the populations come from f);
+ *   f:      caller-owned device array of V*Z values in the cfg precision
+ *           (f[v*Z + s], v = k*Q_xi + j), advanced in place by nsteps TVD-RK3
+ *           steps (Eq. rk3 of L_Sod, Eq. L_Sod);
+ *   stream: cudaStream_t as void* (NULL = legacy default stream).
+ *
+ * Limits: Q_xi*Q_L <= RSLB_NOALLOC_MAX_VELOCITIES, Q_L <= 8, and three stage
+ * buffers of V x ceil32(Z) values plus O(V) tables must fit the static array;
+ * larger problems are rejected with RSLB_ERR_UNSUPPORTED before any device
+ * work.  The call synchronises the stream before returning and reports device
+ * errors (RSLB_ERR_NONPHYSICAL) directly.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call shares
+ * the one array, which keeps the previous call's contents (each call clears
+ * what it needs), so calls that overlap on the GPU -- from several threads or
+ * streams -- race on it and must be serialised by the caller.
+ * Errors: RSLB_ERR_ARG, RSLB_ERR_CFL, RSLB_ERR_STIFF, RSLB_ERR_UNSUPPORTED,
+ * RSLB_ERR_CUDA, RSLB_ERR_NONPHYSICAL.
+ */
+#define RSLB_NOALLOC_SCRATCH_BYTES (64ull << 20)
+#define RSLB_NOALLOC_MAX_VELOCITIES 1024
+int rslb_sod_step_noalloc(const rslb_config* cfg, void* f, int nsteps, void* stream);
+
 /* Release everything owned by h (synchronises its stream).  NULL is a no-op. */
 void rslb_destroy(rslb_handle* h);
 

@@ -194,3 +194,27 @@ class Sod:
 
     def __exit__(self, *a):
         self.close()
+
+
+def sod_step_noalloc(f_ptr, nsteps, Z, Q_xi, Q_L=3, N_Omega=None, z_min=-1.0, z_max=1.0,
+                     precision="f32", bc="outflow", tau_mode="const", tau=1e-3, tau_AW0=0.0,
+                     lambda_ref=1.0, dt=5e-4, left=(1.0, 1.0, 0.0), right=(0.125, 0.8, 0.0),
+                     stream=None):
+    """Advance caller-owned device populations (pointer ``f_ptr``, V*Z values of the
+    given precision) by ``nsteps`` steps with ``rslb_sod_step_noalloc``, which
+    allocates no device memory (for callers that may not allocate)."""
+    L = load()
+    fn = L.rslb_sod_step_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    if N_Omega is None:
+        N_Omega = min(Q_xi - 1, 5)
+    if precision not in ("f32", "fp32", "f64", "fp64", F32, F64):
+        raise ValueError("precision must be 'f32' or 'f64'")
+    fp64 = precision in ("f64", "fp64", F64)
+    cfg = Config(int(Z), z_min, z_max, int(Q_xi), int(Q_L), int(N_Omega), F64 if fp64 else F32,
+                 BC[bc] if isinstance(bc, str) else int(bc),
+                 TAU[tau_mode] if isinstance(tau_mode, str) else int(tau_mode),
+                 tau, tau_AW0, lambda_ref, dt, left[0], left[1], left[2],
+                 right[0], right[1], right[2], None, None, None, 0)
+    _check(fn(ctypes.byref(cfg), ctypes.c_void_p(f_ptr), int(nsteps), _stream_ptr(stream)))
