@@ -655,20 +655,24 @@ static void kl_fill(const orc_model* md, double* K) {
  *                                          + (m-1)/(2m-1) P_{m-2}(xi_j') ]. */
 static void kp_fill(const orc_model* md, double* K) {
   const int Q = md->Q_xi;
+  /* table P[m][j] = P_m(xi_j), m = 0 .. Q+1 (values of Sec. III C) */
+  double* P = (double*)malloc(sizeof(double) * (size_t)(Q + 2) * Q);
+  for (int m = 0; m < Q + 2; ++m)
+    for (int j = 0; j < Q; ++j) P[(size_t)m * Q + j] = orc_legendre(m, md->xi[j]);
+#define PM(m, j) ((m) < 0 ? 0.0 : P[(size_t)(m) * Q + (j)])
   for (int j = 0; j < Q; ++j)
     for (int jp = 0; jp < Q; ++jp) {
-      double xj = md->xi[j], xp = md->xi[jp];
       double s1 = 0.0, s2 = 0.0;
       for (int m = 1; m <= Q - 3; ++m)
-        s1 += m * (m + 1.0) * (m + 2.0) / (2.0 * (2.0 * m + 3.0)) *
-              orc_legendre(m, xj) * orc_legendre(m + 2, xp);
+        s1 += m * (m + 1.0) * (m + 2.0) / (2.0 * (2.0 * m + 3.0)) * PM(m, j) * PM(m + 2, jp);
       for (int m = 1; m <= Q - 1; ++m)
-        s2 += m * (m + 1.0) / 2.0 * orc_legendre(m, xj) *
-              ((2.0 * m + 1.0) * orc_legendre(m, xp) /
-                   ((2.0 * m - 1.0) * (2.0 * m + 3.0)) +
-               (m - 1.0) / (2.0 * m - 1.0) * orc_legendre(m - 2, xp));
+        s2 += m * (m + 1.0) / 2.0 * PM(m, j) *
+              ((2.0 * m + 1.0) * PM(m, jp) / ((2.0 * m - 1.0) * (2.0 * m + 3.0)) +
+               (m - 1.0) / (2.0 * m - 1.0) * PM(m - 2, jp));
       K[j * Q + jp] = md->wxi[j] * (s1 - s2);
     }
+#undef PM
+  free(P);
 }
 
 int orc_kl_matrix(int Q_L, double* K) {
