@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--tubes", type=int, default=len(TAUS),
                     help="number of the four tau tubes per step (profiling runs use 1)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the batched Bjorken and batched shock-tube side measurements")
+    ap.add_argument("--bj-steps", type=int, default=20)
+    ap.add_argument("--batch-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -157,6 +161,71 @@ def recorded_traffic(kernel):
     return None
 
 
+HBARC_GEV_FM = 0.1973269804
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def _timed(stream, fn, n):
+    import torch
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn(n)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def bench_bjorken(stream, steps=None):
+    """Batched Bjorken flow: 16384 runs, Q_xi integer-uniform in [8, 512], Q_L = 3,
+    eta/s log-uniform [0.01, 10], T0 uniform [0.3, 0.6] GeV, tau0 = 0.5 fm/c
+    (nondimensional tau from 1), dtau = 1e-3.  One step = one RK3 step of every run."""
+    from paper_1612_01287_gb300 import Bjorken
+    steps = steps or ARGS.bj_steps
+    qxi, eta_s, T0 = workloads.bjorken_batch()
+    taus = 5 * HBARC_GEV_FM * eta_s / (0.5 * T0)
+    cv = 3 * int(qxi.sum())
+    flops = 3 * 2 * 3 * float((qxi.astype(np.float64) ** 2).sum())  # K^P contraction only
+    out = {"runs": len(qxi), "cv_per_step": cv, "kp_flops_per_step": flops}
+    for mode in ("simt",):
+        with Bjorken(qxi, "parton", taus, Q_L=3, precision="f32", kp_mode=mode, dtau=1e-3,
+                     stream=stream) as b:
+            b.step(1)
+            ms = _timed(stream, b.step, steps) / steps
+            o = b.read()
+            if not np.all(np.isfinite(o["E"])):
+                raise RuntimeError("non-finite Bjorken state")
+        out[mode] = {"value": cv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "steps": steps, "kp_tflops": flops / (ms * 1e-3) / 1e12,
+                     "fp32_peak_tflops": FP32_PEAK_TFLOPS}
+    return out
+
+
+def bench_sod_batch(stream, steps=None):
+    """Uneven batch of 4096 shock tubes (Z log-uniform [256, 8192], Q_xi in
+    {8, 20, 50, 100, 200}, Q_L = 3, tau log-uniform [1e-4, 10], pressure ratio
+    [2, 20]); FP32; timed over the first batch steps, when every run is active."""
+    from paper_1612_01287_gb300 import SodBatch
+    steps = steps or ARGS.batch_steps
+    runs = workloads.sod_sweep()
+    t0 = time.perf_counter()
+    with SodBatch(runs, precision="f32", autotune=True, stream=stream) as b:
+        init_s = time.perf_counter() - t0
+        cv = sum(r["Z"] * 3 * r["Q_xi"] for r in runs)
+        b.step(1)
+        ms = _timed(stream, b.step, steps) / steps
+        tuning = b.tuning()
+        total = b.total_cv_updates
+        m = b.moments(0)
+        if not np.all(np.isfinite(m["E"])):
+            raise RuntimeError("non-finite batched state")
+    return {"runs": len(runs), "value": cv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "steps": steps, "cv_per_step": cv, "init_s": init_s,
+            "tuning": [{"V": V, "tile_cells": B, "ctas_per_sm": K} for V, B, K in tuning],
+            "cv_updates_to_t_end": total}
+
+
 def cpu_baseline(w, dt, steps=20, cells=2048):
     """The FP64 oracle on the host cores, on a bounded sample of the workload:
     `cells` cells around the membrane of one tube, all 600 velocities."""
@@ -236,7 +305,10 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     w = workloads.sod_large()
     dt = workload_dt(w)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library captures its RK steps into a CUDA graph
+    # on non-default streams
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     tubes = [Sod(Z=w["Z"], Q_xi=w["Q_xi"], Q_L=w["Q_L"], N_Omega=w["N_Omega"], bc=w["bc"],
                  tau=tau, dt=dt, left=w["left"], right=w["right"], precision="f32",
                  stream=stream) for tau in TAUS[:max(1, min(args.tubes, len(TAUS)))]]
@@ -321,8 +393,17 @@ def run_ours(args, rank, world, local_rank):
             fp64 = {"value": V * Z / (fms * 1e-3), "unit": UNIT, "ms_per_tube_step": fms,
                     "note": "one tube, FP64 everywhere; bound by the FP64 pipe, not HBM"}
 
+    B_tile = tubes[0].launch_info()[0]
+    kname = "sod32_stage_kernel" if B_tile == 28 else "sod_stage_kernel<float,%d>" % B_tile
     for t in tubes:
         t.close()
+    extras = {}
+    if rank == 0 and not args.no_side:
+        for name, fn in (("bjorken", bench_bjorken), ("sod_batch", bench_sod_batch)):
+            try:
+                extras[name] = fn(stream)
+            except Exception as exc:  # a side measurement never sinks the headline line
+                extras[name] = {"error": repr(exc)[:300]}
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -339,10 +420,10 @@ def run_ours(args, rank, world, local_rank):
         "config": config_dict(w, dt, len(tubes)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
-                     "kernel": "sod_stage_kernel<float,32>",
+                     "kernel": kname,
                      "algorithmic_bytes_per_launch": BYTES_PER_CV_STEP_F32 / 3.0 * V * Z,
                      "avg_launch_ms": per_launch_ms,
-                     "traffic": recorded_traffic("sod_stage_kernel<float,32>")},
+                     "traffic": recorded_traffic(kname)},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": 14 * Z * 8, "steps": e2e_steps,
                 "note": "per step: pinned host populations -> device (rslb_set_state), one "
@@ -351,6 +432,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "fp64": fp64,
     }
+    line.update(extras)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, dt)
     print(json.dumps(line), flush=True)
@@ -359,8 +441,13 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+ARGS = None
+
+
 def main():
+    global ARGS
     args = parse()
+    ARGS = args
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)

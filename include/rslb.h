@@ -114,9 +114,9 @@ typedef struct rslb_config {
   const double* n0;
   const double* T0;
   const double* beta0;
-  /* Cells per CTA tile of the stage kernel: 0 = automatic (largest tile that
-   * keeps two CTAs per SM); otherwise 32 or 16 (RSLB_F32), 16 or 8
-   * (RSLB_F64).  A tuning knob; results do not depend on it. */
+  /* Cells per CTA tile of the stage kernel: 0 = automatic; otherwise 28 (the
+   * packed FP32x2 kernel: V >= 128, N_Omega <= 7), 32 or 16 (RSLB_F32), 16 or
+   * 8 (RSLB_F64).  A tuning knob; results agree to rounding. */
   int tile_cells;
 } rslb_config;
 
@@ -130,7 +130,8 @@ typedef struct rslb_handle rslb_handle;
  * rslb_destroy.
  * Errors: RSLB_ERR_ARG (bad cfg), RSLB_ERR_CFL (max|xi| dt/dz >= 1),
  * RSLB_ERR_STIFF (RSLB_TAU_CONST and dt >= tau), RSLB_ERR_UNSUPPORTED
- * (V = Q_xi*Q_L too large for one tile), RSLB_ERR_ALLOC, RSLB_ERR_CUDA,
+ * (V = Q_xi*Q_L too large for one tile of 16 (FP32) or 8 (FP64) cells),
+ * RSLB_ERR_ALLOC, RSLB_ERR_CUDA,
  * RSLB_ERR_NONPHYSICAL (an initial state with n <= 0, T <= 0 or |beta| >= 1).
  */
 int rslb_init(rslb_handle** h, const rslb_config* cfg, void* stream);
@@ -174,6 +175,10 @@ int rslb_set_state(rslb_handle* h, const void* f, int on_device);
 /* Simulation time and step count of the handle (host-side bookkeeping). */
 int rslb_time(const rslb_handle* h, double* t, long long* steps);
 
+/* The stage kernel the handle launches: cells per CTA tile (28 = packed
+ * FP32x2 kernel) and threads per CTA.  Errors: RSLB_ERR_ARG. */
+int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* threads);
+
 /*
  * Allocation-free shock-tube step (no counterpart in the paper; a service for
  * callers that cannot allocate device memory).
@@ -214,6 +219,161 @@ int rslb_sod_step_noalloc(const rslb_config* cfg, void* f, int nsteps, void* str
 
 /* Release everything owned by h (synchronises its stream).  NULL is a no-op. */
 void rslb_destroy(rslb_handle* h);
+
+/* ------------------------------------------------------------------------ */
+/* Batches of independent shock tubes (uneven Z, Q_xi, tau, states).         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct rslb_sod_run {
+  int Z;                  /* cells */
+  int Q_xi;               /* polar nodes */
+  double tau;             /* constant relaxation time > 0 */
+  double nL, TL, nR, TR;  /* chambers at rest (Sec. IV A) */
+  double t_end;           /* final time > 0 */
+} rslb_sod_run;
+
+typedef struct rslb_sod_batch_opts {
+  int Q_L;             /* radial nodes (shared) */
+  int N_Omega;         /* -1: min(Q_xi - 1, 5) for each run */
+  int precision;       /* RSLB_F32 or RSLB_F64 */
+  int bc;              /* RSLB_BC_FIXED_EQ or RSLB_BC_OUTFLOW */
+  double z_min, z_max; /* domain of every run */
+  double cfl;          /* dt <= cfl dz / max|xi| (Eq. CFL) */
+  double dt_over_tau;  /* dt <= dt_over_tau * tau (explicit RK3 limit) */
+  int autotune;        /* 1: time the candidate tile kernels per velocity class */
+} rslb_sod_batch_opts;
+
+typedef struct rslb_sod_batch rslb_sod_batch;
+
+/*
+ * Set up nruns shock tubes.  Each run gets dt = t_end / ceil(t_end / dt_max)
+ * with dt_max = min(cfl dz / max|xi|, dt_over_tau * tau), i.e. it reaches
+ * t_end exactly after its own number of steps.  Runs are grouped by velocity
+ * count; each group is advanced by one persistent launch per RK stage that
+ * walks the tiles of its runs (runs with fewer steps drop out as they
+ * finish).  With autotune, the tile kernel and CTAs per SM of each group are
+ * chosen by timing the candidates on the actual state.
+ * Errors: RSLB_ERR_ARG, RSLB_ERR_UNSUPPORTED, RSLB_ERR_ALLOC, RSLB_ERR_CUDA.
+ */
+int rslb_sod_batch_init(rslb_sod_batch** b, const rslb_sod_run* runs, int nruns,
+                        const rslb_sod_batch_opts* opts, void* stream);
+
+/*
+ * Enqueue nsteps batch steps (each active run advances one RK3 step, Eq. rk3;
+ * runs stop at their own step count).  Steps are replayed from a captured
+ * CUDA graph on non-default streams.  Errors: RSLB_ERR_ARG, RSLB_ERR_CUDA.
+ */
+int rslb_sod_batch_step(rslb_sod_batch* b, int nsteps);
+
+/* Batch bookkeeping: the largest per-run step count, steps enqueued so far,
+ * and the cell-velocity updates all runs perform in total to their t_end. */
+int rslb_sod_batch_info(const rslb_sod_batch* b, long long* max_steps, long long* steps_done,
+                        double* total_cv_updates);
+
+/* Per-run step count and time step. */
+int rslb_sod_batch_run_info(const rslb_sod_batch* b, int run, long long* nsteps, double* dt);
+
+/* The tuner's choice for velocity group g (groups in ascending V): tile
+ * width (cells per CTA) and CTAs per SM; returns RSLB_ERR_ARG past the last. */
+int rslb_sod_batch_tuning(const rslb_sod_batch* b, int g, int* V, int* tile_cells,
+                          int* ctas_per_sm);
+
+/* Moments of one run (as rslb_moments; out: host, RSLB_NFIELDS * Z). */
+int rslb_sod_batch_moments(rslb_sod_batch* b, int run, double* out);
+
+void rslb_sod_batch_destroy(rslb_sod_batch* b);
+
+/* ------------------------------------------------------------------------ */
+/* Boost-invariant (Bjorken) flow, batched over independent runs (Sec. V).  */
+/* ------------------------------------------------------------------------ */
+
+#define RSLB_GAS_PARTON 0 /* n_eq = P^{3/4}, T = P^{1/4} (Eqs. bjorken_mu0,
+                             bjorken_tauAW0) */
+#define RSLB_GAS_IDEAL 1  /* n_eq = n, T = P/n (Eq. bjorken_tauAW_mu) */
+
+#define RSLB_KP_SIMT 0   /* K^P contraction on the CUDA cores in the working
+                            precision (FP64 or FP32) */
+#define RSLB_KP_BF16X3 1 /* reserved: BF16 hi/lo split on the tensor cores
+                            (not available: its ~1e-5 error per product is
+                            at the FP32 tolerance; see RSLB_KP_TF32X3) */
+#define RSLB_KP_TF32X3 2 /* K^P contraction on the tcgen05 tensor cores
+                            (kind::tf32, accumulators in tensor memory):
+                            both operands split x = hi + lo with
+                            hi = tf32(x), products hi*hi + hi*lo + lo*hi,
+                            FP32 accumulation.  RSLB_F32 only, Q_L <= 4. */
+
+/* Number of per-run outputs of rslb_bjorken_read, in this order:
+ * tau, n = N^tau, E = T^{tau tau}, P = E/3, T, Pi = P_L - P,
+ * P_L = T^{eta eta}, P_T = (E - P_L)/2   (Eqs. bjorken_SET, bjorken_P) */
+#define RSLB_BJ_NOUT 8
+
+typedef struct rslb_bjorken_run {
+  int Q_xi;       /* polar nodes of this run, 2 .. 512 */
+  int gas;        /* RSLB_GAS_* */
+  double tau_AW0; /* relaxation scale of Eq. bjorken_tauAW (units of tau0);
+                     <= 0 or infinite: collisionless */
+} rslb_bjorken_run;
+
+typedef struct rslb_bjorken_opts {
+  int Q_L;        /* radial nodes, 1..8 (shared by all runs) */
+  int precision;  /* RSLB_F32 or RSLB_F64 */
+  int kp_mode;    /* RSLB_KP_* */
+  double tau0;    /* initial proper time, > 0 (the paper's nondimensional 1) */
+  double dtau;    /* time step, > 0 */
+} rslb_bjorken_opts;
+
+typedef struct rslb_bjorken rslb_bjorken;
+
+/*
+ * Set up nruns independent Bjorken runs (Secs. II F, III, V A): each starts
+ * from the isotropic equilibrium f = e^{-p}/(8 pi) at tau = tau0
+ * (Eq. bjorken_f0), i.e. populations f_jk = w_j w_k / 4 (Eq. fjk).  Builds
+ * the K^P matrix (Eq. K_leg_disc) of every distinct Q_xi and K^L
+ * (Eq. K_lag_disc) on the device in FP64.  runs: caller-owned host array of
+ * nruns entries, read during the call.
+ * Errors: RSLB_ERR_ARG, RSLB_ERR_STIFF (dtau >= the initial tau_AW of a run),
+ * RSLB_ERR_UNSUPPORTED, RSLB_ERR_ALLOC, RSLB_ERR_CUDA.
+ */
+int rslb_bjorken_init(rslb_bjorken** b, const rslb_bjorken_run* runs, int nruns,
+                      const rslb_bjorken_opts* opts, void* stream);
+
+/*
+ * Enqueue nsteps TVD-RK3 steps (Eq. rk3) of L_Bjorken (Eq. L_Bjorken) for
+ * every run, with stage times tau_n, tau_n + dtau, tau_n + dtau/2.  Per
+ * stage: moments, equilibrium (gas law), f^eq at u = 0 (Eq. Bjorken_MB via
+ * Eqs. feq_trunc, fjk), the K^L term, the K^P contraction, relaxation and
+ * the RK combination.  Asynchronous.  Errors: RSLB_ERR_ARG, RSLB_ERR_CUDA.
+ */
+int rslb_bjorken_step(rslb_bjorken* b, int nsteps);
+
+/*
+ * Per-run observables of the current state: out[r*RSLB_BJ_NOUT + i] in the
+ * callers' run order (see RSLB_BJ_NOUT).  out: caller-owned host memory, or
+ * device memory if out_on_device.  Synchronises.  Errors: RSLB_ERR_ARG,
+ * RSLB_ERR_CUDA, RSLB_ERR_NONPHYSICAL (a run with P <= 0 or non-finite).
+ */
+int rslb_bjorken_read(rslb_bjorken* b, double* out, int out_on_device);
+
+/*
+ * Populations of all runs, concatenated in the callers' run order, each run
+ * f[k*Q_xi + j] (Q_L*Q_xi values), in the handle's precision; host memory.
+ * rslb_bjorken_get_state synchronises.  Errors: RSLB_ERR_ARG, RSLB_ERR_CUDA.
+ */
+int rslb_bjorken_get_state(rslb_bjorken* b, void* f);
+int rslb_bjorken_set_state(rslb_bjorken* b, const void* f);
+
+/*
+ * The xi-derivative contraction alone: y_r = K^P f_r (Eq. K_leg_disc applied
+ * to the radial columns of every run, y[k*Q_xi + j] = sum_j' K^P_{j j'}
+ * f[k*Q_xi + j']) on the current state, computed by the handle's tensor-core
+ * path, written like rslb_bjorken_get_state (FP32, callers' run order, host
+ * memory).  Synchronises.  Errors: RSLB_ERR_ARG, RSLB_ERR_UNSUPPORTED
+ * (kp_mode other than RSLB_KP_TF32X3), RSLB_ERR_CUDA.
+ */
+int rslb_bjorken_kp_apply(rslb_bjorken* b, void* y);
+
+/* Release everything owned by b (synchronises).  NULL is a no-op. */
+void rslb_bjorken_destroy(rslb_bjorken* b);
 
 /* Description of the last failure in the calling thread ("" if none). */
 const char* rslb_last_error(void);

@@ -68,6 +68,7 @@ def load():
         "rslb_get_state": (i, [p, p, i]),
         "rslb_set_state": (i, [p, p, i]),
         "rslb_time": (i, [p, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),
+        "rslb_launch_info": (i, [p, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "rslb_destroy": (None, [p]),
         "rslb_last_error": (ctypes.c_char_p, []),
     }
@@ -178,6 +179,12 @@ class Sod:
         _check(load().rslb_time(self._h, ctypes.byref(t), ctypes.byref(n)))
         return t.value, n.value
 
+    def launch_info(self):
+        """(cells per CTA tile, threads per CTA) of the stage kernel."""
+        B, T = ctypes.c_int(), ctypes.c_int()
+        _check(load().rslb_launch_info(self._h, ctypes.byref(B), ctypes.byref(T)))
+        return B.value, T.value
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             load().rslb_destroy(self._h)
@@ -218,3 +225,240 @@ def sod_step_noalloc(f_ptr, nsteps, Z, Q_xi, Q_L=3, N_Omega=None, z_min=-1.0, z_
                  tau, tau_AW0, lambda_ref, dt, left[0], left[1], left[2],
                  right[0], right[1], right[2], None, None, None, 0)
     _check(fn(ctypes.byref(cfg), ctypes.c_void_p(f_ptr), int(nsteps), _stream_ptr(stream)))
+
+
+BJ_FIELDS = ("tau", "n", "E", "P", "T", "Pi", "PL", "PT")
+GAS = {"parton": 0, "ideal": 1}
+KP = {"simt": 0, "bf16x3": 1, "tf32x3": 2}
+
+
+class BjorkenRun(ctypes.Structure):
+    """Mirror of ``rslb_bjorken_run``."""
+    _fields_ = [("Q_xi", ctypes.c_int), ("gas", ctypes.c_int), ("tau_AW0", ctypes.c_double)]
+
+
+class BjorkenOpts(ctypes.Structure):
+    """Mirror of ``rslb_bjorken_opts``."""
+    _fields_ = [("Q_L", ctypes.c_int), ("precision", ctypes.c_int), ("kp_mode", ctypes.c_int),
+                ("tau0", ctypes.c_double), ("dtau", ctypes.c_double)]
+
+
+def _bj_sigs(L):
+    if getattr(L, "_bj_ready", False):
+        return
+    i, p = ctypes.c_int, ctypes.c_void_p
+    for name, (res, args) in {
+        "rslb_bjorken_init": (i, [ctypes.POINTER(p), ctypes.POINTER(BjorkenRun), i,
+                                  ctypes.POINTER(BjorkenOpts), p]),
+        "rslb_bjorken_step": (i, [p, i]),
+        "rslb_bjorken_read": (i, [p, p, i]),
+        "rslb_bjorken_get_state": (i, [p, p]),
+        "rslb_bjorken_set_state": (i, [p, p]),
+        "rslb_bjorken_kp_apply": (i, [p, p]),
+        "rslb_bjorken_destroy": (None, [p]),
+    }.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    L._bj_ready = True
+
+
+class Bjorken:
+    """A batch of independent boost-invariant runs (``rslb_bjorken``)."""
+
+    def __init__(self, Q_xi, gas="parton", tau_AW0=float("inf"), Q_L=3, precision="f32",
+                 kp_mode="simt", tau0=1.0, dtau=1e-3, stream=None):
+        """Q_xi, gas, tau_AW0: per-run sequences (scalars are broadcast)."""
+        L = load()
+        _bj_sigs(L)
+        Q_xi = np.atleast_1d(np.asarray(Q_xi, dtype=np.int64))
+        n = len(Q_xi)
+        gas = np.broadcast_to(np.asarray([GAS[g] if isinstance(g, str) else int(g)
+                                          for g in np.atleast_1d(gas)]), (n,))
+        t0 = np.broadcast_to(np.atleast_1d(np.asarray(tau_AW0, dtype=np.float64)), (n,))
+        runs = (BjorkenRun * n)()
+        for r in range(n):
+            runs[r].Q_xi = int(Q_xi[r])
+            runs[r].gas = int(gas[r])
+            runs[r].tau_AW0 = float(t0[r])
+        if precision not in ("f32", "fp32", "f64", "fp64", F32, F64):
+            raise ValueError("precision must be 'f32' or 'f64'")
+        self.fp64 = precision in ("f64", "fp64", F64)
+        self.dtype = np.float64 if self.fp64 else np.float32
+        opts = BjorkenOpts(int(Q_L), F64 if self.fp64 else F32,
+                           KP[kp_mode] if isinstance(kp_mode, str) else int(kp_mode),
+                           float(tau0), float(dtau))
+        self.nruns, self.Q_xi, self.Q_L = n, Q_xi.copy(), int(Q_L)
+        self._h = ctypes.c_void_p()
+        _check(L.rslb_bjorken_init(ctypes.byref(self._h), runs, n, ctypes.byref(opts),
+                                   _stream_ptr(stream)))
+
+    def step(self, nsteps=1):
+        _check(load().rslb_bjorken_step(self._h, int(nsteps)))
+
+    def read(self):
+        out = np.zeros((self.nruns, len(BJ_FIELDS)))
+        _check(load().rslb_bjorken_read(self._h, _ptr(out), 0))
+        return {k: out[:, i] for i, k in enumerate(BJ_FIELDS)}
+
+    def read_into(self, ptr, on_device):
+        _check(load().rslb_bjorken_read(self._h, ctypes.c_void_p(ptr), int(on_device)))
+
+    def get_state(self):
+        f = np.zeros(int(self.Q_L * self.Q_xi.sum()), dtype=self.dtype)
+        _check(load().rslb_bjorken_get_state(self._h, _ptr(f)))
+        return f
+
+    def set_state(self, f):
+        f = np.ascontiguousarray(f, dtype=self.dtype)
+        _check(load().rslb_bjorken_set_state(self._h, _ptr(f)))
+
+    def kp_apply(self):
+        """K^P f of every run's current state (tensor-core path), like get_state."""
+        y = np.zeros(int(self.Q_L * self.Q_xi.sum()), dtype=np.float32)
+        _check(load().rslb_bjorken_kp_apply(self._h, _ptr(y)))
+        return y
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().rslb_bjorken_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class SodRun(ctypes.Structure):
+    """Mirror of ``rslb_sod_run``."""
+    _fields_ = [("Z", ctypes.c_int), ("Q_xi", ctypes.c_int), ("tau", ctypes.c_double),
+                ("nL", ctypes.c_double), ("TL", ctypes.c_double), ("nR", ctypes.c_double),
+                ("TR", ctypes.c_double), ("t_end", ctypes.c_double)]
+
+
+class SodBatchOpts(ctypes.Structure):
+    """Mirror of ``rslb_sod_batch_opts``."""
+    _fields_ = [("Q_L", ctypes.c_int), ("N_Omega", ctypes.c_int), ("precision", ctypes.c_int),
+                ("bc", ctypes.c_int), ("z_min", ctypes.c_double), ("z_max", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("dt_over_tau", ctypes.c_double),
+                ("autotune", ctypes.c_int)]
+
+
+def _batch_sigs(L):
+    if getattr(L, "_batch_ready", False):
+        return
+    i, p, ll, d = ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double
+    P = ctypes.POINTER
+    for name, (res, args) in {
+        "rslb_sod_batch_init": (i, [P(p), P(SodRun), i, P(SodBatchOpts), p]),
+        "rslb_sod_batch_step": (i, [p, i]),
+        "rslb_sod_batch_info": (i, [p, P(ll), P(ll), P(d)]),
+        "rslb_sod_batch_run_info": (i, [p, i, P(ll), P(d)]),
+        "rslb_sod_batch_tuning": (i, [p, i, P(i), P(i), P(i)]),
+        "rslb_sod_batch_moments": (i, [p, i, p]),
+        "rslb_sod_batch_destroy": (None, [p]),
+    }.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    L._batch_ready = True
+
+
+class SodBatch:
+    """Many independent shock tubes advanced together (``rslb_sod_batch``).
+
+    ``runs``: sequence of dicts with keys Z, Q_xi, tau, t_end and optionally
+    nL, TL, nR, TR (default: the chambers of Sec. IV A)."""
+
+    def __init__(self, runs, Q_L=3, N_Omega=-1, precision="f32", bc="outflow", z_min=-1.0,
+                 z_max=1.0, cfl=0.5, dt_over_tau=0.5, autotune=True, stream=None):
+        L = load()
+        _batch_sigs(L)
+        n = len(runs)
+        arr = (SodRun * n)()
+        for r, R in enumerate(runs):
+            arr[r] = SodRun(int(R["Z"]), int(R["Q_xi"]), float(R["tau"]), float(R.get("nL", 1.0)),
+                            float(R.get("TL", 1.0)), float(R.get("nR", 0.125)),
+                            float(R.get("TR", 0.8)), float(R["t_end"]))
+        if precision not in ("f32", "fp32", "f64", "fp64", F32, F64):
+            raise ValueError("precision must be 'f32' or 'f64'")
+        self.fp64 = precision in ("f64", "fp64", F64)
+        opts = SodBatchOpts(int(Q_L), int(N_Omega), F64 if self.fp64 else F32,
+                            BC[bc] if isinstance(bc, str) else int(bc), float(z_min),
+                            float(z_max), float(cfl), float(dt_over_tau), int(bool(autotune)))
+        self.nruns = n
+        self.Z = [int(R["Z"]) for R in runs]
+        self._h = ctypes.c_void_p()
+        _check(L.rslb_sod_batch_init(ctypes.byref(self._h), arr, n, ctypes.byref(opts),
+                                     _stream_ptr(stream)))
+
+    def step(self, nsteps=1):
+        _check(load().rslb_sod_batch_step(self._h, int(nsteps)))
+
+    def run_to_end(self):
+        self.step(self.max_steps - self.steps_done)
+
+    def _info(self):
+        a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
+        _check(load().rslb_sod_batch_info(self._h, ctypes.byref(a), ctypes.byref(b),
+                                          ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    @property
+    def max_steps(self):
+        return self._info()[0]
+
+    @property
+    def steps_done(self):
+        return self._info()[1]
+
+    @property
+    def total_cv_updates(self):
+        return self._info()[2]
+
+    def run_info(self, r):
+        n, dt = ctypes.c_longlong(), ctypes.c_double()
+        _check(load().rslb_sod_batch_run_info(self._h, int(r), ctypes.byref(n), ctypes.byref(dt)))
+        return n.value, dt.value
+
+    def tuning(self):
+        """[(V, tile_cells, ctas_per_sm)] per velocity group."""
+        out, g = [], 0
+        L = load()
+        while True:
+            V, B, K = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            if L.rslb_sod_batch_tuning(self._h, g, ctypes.byref(V), ctypes.byref(B),
+                                       ctypes.byref(K)) != OK:
+                return out
+            out.append((V.value, B.value, K.value))
+            g += 1
+
+    def moments(self, r):
+        out = np.zeros((len(FIELDS), self.Z[r]))
+        _check(load().rslb_sod_batch_moments(self._h, int(r), _ptr(out)))
+        return {k: out[i] for i, k in enumerate(FIELDS)}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().rslb_sod_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,840 @@
+// bjorken.cu -- batched boost-invariant (Bjorken) flow of the R-SLB method
+// (Secs. II F, III, V): many independent homogeneous runs, each a vector of
+// Q_L x Q_xi populations, integrated with TVD-RK3 (Eq. rk3) of L_Bjorken
+// (Eq. L_Bjorken).
+//
+// Runs are grouped by Q_xi.  One CTA integrates a block of R runs that share
+// Q_xi for all requested steps with the whole state in shared memory, laid
+// out [j][r][k] so that the K^P contraction
+//   Y[j][r][k] = sum_j' K^P[j][j'] f[j'][r][k]
+// is a small GEMM: each thread owns rows j and all (r, k) columns of a block of
+// runs, streams K^P^T[j'][j] from global memory (coalesced, L2-resident per
+// group) and reads f[j'][.][.] as a broadcast.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rslb.h"
+#include "host_common.h"
+#include "rslb_device.cuh"
+#include "bjorken.cuh"
+
+namespace rslb {
+
+constexpr int kBjThreads = 256;
+constexpr int kBjMaxQ = 512;
+constexpr int kBjMaxQL = 8;
+constexpr int kTcMaxCols = 80;  // MMA N of a tensor-core block (two CTAs per SM)
+
+// Per-block descriptor (one CTA).
+struct BjBlock {
+  int Q;      // polar nodes
+  int first;  // index of the first run in sorted order
+  int R;      // runs in this block
+  int qidx;   // index of the distinct-Q tables
+};
+
+// Tables of one distinct Q_xi.
+struct BjQTab {
+  long long kp_off;  // offset of K^P^T (Q x Q, [j'][j]) in the K pool
+  long long xi_off;  // offset of xi_j, w_j in the node pool
+};
+
+template <typename T>
+struct BjArgs {
+  const BjBlock* blocks;
+  const BjQTab* qtab;
+  const T* kpool;        // K^P^T matrices
+  const double* npool;   // [xi(Q) | w(Q)] per distinct Q
+  const long long* roff;  // state offset of each run (sorted order)
+  const double* tau_aw0;  // per run (sorted order); <= 0: collisionless
+  const int* gas;         // per run (sorted order)
+  T* state;               // all runs, each [k][j]
+  const double* xk;       // [QL]
+  const double* wk;       // [QL]
+  const double* KL;       // [QL][QL]
+  int QL;
+  int nsteps;
+  double tau_start, dtau;
+  int* err;
+};
+
+__device__ __forceinline__ void bj_report(int* err, int code, int run) {
+  if (atomicCAS(err, 0, code) == 0) err[1] = run;
+}
+
+// ---------------------------------------------------------------------------
+// K^P of Eq. K_leg_disc, built in FP64 on the device; thread per (j, j').
+//   K^P_{j,j'} = w_j sum_{m=1}^{Q-3} m(m+1)(m+2)/(2(2m+3)) P_m(xi_j) P_{m+2}(xi_j')
+//              - w_j sum_{m=1}^{Q-1} m(m+1)/2 P_m(xi_j) [ (2m+1) P_m(xi_j') /
+//                ((2m-1)(2m+3)) + (m-1)/(2m-1) P_{m-2}(xi_j') ]
+// Output transposed: KT[j'][j].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void bj_kp_kernel(int Q, const double* __restrict__ xw, T* KT) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Q * Q) return;
+  const int j = idx / Q, jp = idx - j * Q;
+  KT[(size_t)jp * Q + j] = T(kp_entry(Q, xw, j, jp));
+}
+
+// K^L of Eq. K_lag_disc (Q_L x Q_L), FP64, one thread per entry.
+__global__ void bj_kl_kernel(int QL, const double* __restrict__ xk, const double* __restrict__ wk,
+                             double* KL) {
+  const int k = threadIdx.x / QL, kp = threadIdx.x % QL;
+  if (k >= QL) return;
+  auto lag = [](int l, double x) {
+    if (l < 0) return 0.0;
+    double a = 1.0, b = 3.0 - x;
+    if (l == 0) return a;
+    for (int n = 1; n < l; ++n) {
+      const double c = ((2.0 * n + 3.0 - x) * b - (n + 2.0) * a) / (n + 1.0);
+      a = b;
+      b = c;
+    }
+    return b;
+  };
+  double s = 0.0;
+  for (int l = 1; l <= QL - 1; ++l)
+    s += lag(l, xk[k]) * ((l + 2.0) * lag(l - 1, xk[kp]) - l * lag(l, xk[kp])) /
+         ((l + 1.0) * (l + 2.0));
+  KL[k * QL + kp] = wk[k] * s;
+}
+
+// ---------------------------------------------------------------------------
+// The batched step kernel (SIMT contraction).
+// Shared memory: three copies of the block state, [j][r][k] with row stride
+// RS = RP * QL (RP = R rounded up to RB; padded runs stay zero):
+//   stage 1 reads F, writes A; stage 2 reads A (and F), writes B;
+//   stage 3 reads B (and F), writes F.
+// A stage never writes the array it contracts, so any thread may finish its
+// outputs while others still read.
+// ---------------------------------------------------------------------------
+template <typename T, int RB>
+__global__ void __launch_bounds__(kBjThreads)
+bj_step_kernel(BjArgs<T> a, int block0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BjBlock blk = a.blocks[block0 + blockIdx.x];
+  const int Q = blk.Q, R = blk.R, QL = a.QL;
+  const int RP = (R + RB - 1) / RB * RB;
+  const int RS = RP * QL;
+  const size_t NS = (size_t)Q * RS;
+  T* F = reinterpret_cast<T*>(smem_raw);
+  T* Abuf = F + NS;
+  T* Bbuf = Abuf + NS;
+  double* rs = reinterpret_cast<double*>(smem_raw + ((3 * NS * sizeof(T) + 15) & ~size_t(15)));
+  double* sRate = rs;         // [RP] 1/tau_AW (0: collisionless)
+  double* sNeq = rs + RP;     // [RP] n_eq/4
+  double* sOneMT = rs + 2 * RP;  // [RP] 1 - T
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* xw = a.npool + a.qtab[blk.qidx].xi_off;
+  const T* KT = a.kpool + a.qtab[blk.qidx].kp_off;
+
+  // load state: global run r [k][j] -> F[j][r][k]; padded runs are zero
+  for (int idx = tid; idx < (int)NS; idx += kBjThreads) {
+    const int j = idx / RS, rk = idx - j * RS, r = rk / QL, k = rk - r * QL;
+    T v = T(0);
+    if (r < R) v = a.state[a.roff[blk.first + r] + (size_t)k * Q + j];
+    F[idx] = v;
+    Abuf[idx] = T(0);
+    Bbuf[idx] = T(0);
+  }
+  __syncthreads();
+
+  const int nunits = Q * (RP / RB);
+  for (int step = 0; step < a.nsteps; ++step) {
+    const double tn = a.tau_start + step * a.dtau;
+    for (int stage = 0; stage < 3; ++stage) {
+      const T* S = (stage == 0) ? F : (stage == 1 ? Abuf : Bbuf);
+      T* D = (stage == 0) ? Abuf : (stage == 1 ? Bbuf : F);
+      const double tau = tn + (stage == 0 ? 0.0 : (stage == 1 ? a.dtau : 0.5 * a.dtau));
+      // ---- moments and equilibrium per run: warp per run ----
+      for (int r = warp; r < RP; r += kBjThreads / 32) {
+        double E = 0.0, N = 0.0;
+        if (r < R) {
+          for (int e = lane; e < Q * QL; e += 32) {
+            const int j = e / QL, k = e - j * QL;
+            const double fv = (double)S[(size_t)j * RS + r * QL + k];
+            N += fv;
+            E += fv * a.xk[k];
+          }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+          E += __shfl_xor_sync(0xffffffffu, E, o);
+          N += __shfl_xor_sync(0xffffffffu, N, o);
+        }
+        if (lane == 0) {
+          double rate = 0.0, neq4 = 0.0, omt = 0.0;
+          if (r < R) {
+            const int gr = blk.first + r;
+            const double P = E / 3.0;
+            const double t0 = a.tau_aw0[gr];
+            const bool coll = t0 > 0.0 && isfinite(t0);
+            if (!(P > 0.0) || !isfinite(P) || (a.gas[gr] == RSLB_GAS_IDEAL && !(N > 0.0))) {
+              bj_report(a.err, RSLB_ERR_NONPHYSICAL, gr);
+            } else if (coll) {
+              double T_, n_eq, tau_aw;
+              if (a.gas[gr] == RSLB_GAS_PARTON) {
+                T_ = sqrt(sqrt(P));
+                n_eq = P / T_;  // P^{3/4}
+                tau_aw = t0 / T_;
+              } else {
+                T_ = P / N;
+                n_eq = N;
+                tau_aw = t0 / T_ * (1.0 - 0.25 * log(N / (T_ * T_ * T_)));
+              }
+              rate = 1.0 / tau_aw;
+              neq4 = 0.25 * n_eq;
+              omt = 1.0 - T_;
+            }
+          }
+          sRate[r] = rate;
+          sNeq[r] = neq4;
+          sOneMT[r] = omt;
+        }
+      }
+      __syncthreads();
+      // ---- L_Bjorken and the RK combination ----
+      const T itau = T(1.0 / tau), dt = T(a.dtau);
+      for (int u = tid; u < nunits; u += kBjThreads) {
+        const int j = u % Q, rb = u / Q;
+        const int r0 = rb * RB;
+        T acc[RB][kBjMaxQL];
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+          for (int k = 0; k < kBjMaxQL; ++k) acc[i][k] = T(0);
+        const T* col = S + r0 * QL;
+        for (int jp = 0; jp < Q; ++jp) {
+          const T kv = KT[(size_t)jp * Q + j];
+          const T* src = col + (size_t)jp * RS;
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int k = 0; k < kBjMaxQL; ++k)
+              if (k < QL) acc[i][k] += kv * src[i * QL + k];
+        }
+        const double xj = xw[j], wj = xw[Q + j];
+        const T xi2 = T(xj * xj);
+        const T* own = S + (size_t)j * RS + r0 * QL;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+          const int r = r0 + i;
+          if (r >= R) continue;
+          T fk[kBjMaxQL];
+#pragma unroll
+          for (int k = 0; k < kBjMaxQL; ++k) fk[k] = (k < QL) ? own[i * QL + k] : T(0);
+          const T rate = T(sRate[r]), neq4 = T(sNeq[r]), omt = T(sOneMT[r]);
+#pragma unroll
+          for (int k = 0; k < kBjMaxQL; ++k) {
+            if (k < QL) {
+              T klf = T(0);
+              for (int kq = 0; kq < QL; ++kq) klf += T(a.KL[k * QL + kq]) * fk[kq];
+              const T feq = neq4 * T(wj * a.wk[k]) * (T(1) + T(3.0 - a.xk[k]) * omt);
+              const T L = (-fk[k] + xi2 * klf + acc[i][k]) * itau - (fk[k] - feq) * rate;
+              const T v = fk[k] + dt * L;
+              const size_t o = (size_t)j * RS + r * QL + k;
+              if (stage == 0) D[o] = v;
+              else if (stage == 1) D[o] = T(0.75) * F[o] + T(0.25) * v;
+              else D[o] = F[o] * T(1.0 / 3.0) + T(2.0 / 3.0) * v;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // write back
+  for (int idx = tid; idx < (int)NS; idx += kBjThreads) {
+    const int j = idx / RS, rk = idx - j * RS, r = rk / QL, k = rk - r * QL;
+    if (r < R) a.state[a.roff[blk.first + r] + (size_t)k * Q + j] = F[idx];
+  }
+}
+
+// Observables per run (warp per run), written in the callers' order.
+template <typename T>
+__global__ void bj_read_kernel(int nruns, int QL, const int* __restrict__ rq,
+                               const long long* __restrict__ roff,
+                               const long long* __restrict__ xoff,
+                               const double* __restrict__ npool, const int* __restrict__ gas,
+                               const int* __restrict__ user, const double* __restrict__ xk,
+                               const T* __restrict__ state, double tau, double* out, int* err) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= nruns) return;
+  const int Q = rq[r];
+  const double* xi = npool + xoff[r];
+  const T* f = state + roff[r];
+  double N = 0.0, E = 0.0, PL = 0.0;
+  for (int v = lane; v < Q * QL; v += 32) {
+    const int k = v / Q, j = v - k * Q;
+    const double fv = (double)f[v];
+    N += fv;
+    E += fv * xk[k];
+    PL += fv * xk[k] * xi[j] * xi[j];
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    N += __shfl_xor_sync(0xffffffffu, N, o);
+    E += __shfl_xor_sync(0xffffffffu, E, o);
+    PL += __shfl_xor_sync(0xffffffffu, PL, o);
+  }
+  if (lane != 0) return;
+  const double P = E / 3.0;
+  const double T_ = (gas[r] == RSLB_GAS_PARTON) ? sqrt(sqrt(P)) : P / N;
+  if (!(P > 0.0) || !isfinite(P) || !isfinite(N)) bj_report(err, RSLB_ERR_NONPHYSICAL, r);
+  double* o = out + (size_t)user[r] * RSLB_BJ_NOUT;
+  o[0] = tau;
+  o[1] = N;
+  o[2] = E;
+  o[3] = P;
+  o[4] = T_;
+  o[5] = PL - P;
+  o[6] = PL;
+  o[7] = 0.5 * (E - PL);
+}
+
+// Initial isotropic state f_jk = w_j w_k / 4 (f = e^{-p}/(8 pi) at tau0).
+template <typename T>
+__global__ void bj_init_kernel(int nruns, int QL, const int* __restrict__ rq,
+                               const long long* __restrict__ roff,
+                               const long long* __restrict__ xoff,
+                               const double* __restrict__ npool, const double* __restrict__ wk,
+                               T* state) {
+  const int r = blockIdx.x;
+  if (r >= nruns) return;
+  const int Q = rq[r];
+  const double* w = npool + xoff[r] + Q;
+  for (int v = threadIdx.x; v < Q * QL; v += blockDim.x) {
+    const int k = v / Q, j = v - k * Q;
+    state[roff[r] + v] = T(0.25 * w[j] * wk[k]);
+  }
+}
+
+}  // namespace rslb
+
+using namespace rslb;
+
+struct rslb_bjorken {
+  int nruns, QL, precision, kp_mode;
+  double tau0, dtau;
+  long long steps;
+  cudaStream_t stream;
+  std::vector<int> user_of_sorted;   // sorted index -> caller index
+  std::vector<long long> roff_h;     // sorted order
+  std::vector<int> rq_h;             // Q per sorted run
+  long long total_state;
+  int nblocks;
+  size_t smem;  // max dynamic smem over blocks
+  std::vector<size_t> block_smem;
+  // device
+  void* state;
+  void* kpool;
+  double* npool;
+  BjBlock* blocks;
+  BjQTab* qtab;
+  long long* roff;
+  long long* xoff;
+  int* rq;
+  double* tau_aw0;
+  int* gas;
+  int* user;
+  double* xk;
+  double* wk;
+  double* KL;
+  int* err;
+  double* out_dev;
+  // tensor-core path (RSLB_KP_TF32X3)
+  BjTcBlock* tcblocks;
+  int ntc;
+  size_t tc_smem;
+  float* kimg;
+  void* F1;
+  void* F2;
+  double* mp[2];
+  int mp_cur;  // which moment buffer describes the state (F0)
+  float* ytmp;
+};
+
+namespace {
+
+void bj_free(rslb_bjorken* b) {
+  if (!b) return;
+  void* ptrs[] = {b->state, b->kpool, b->npool, b->blocks, b->qtab, b->roff, b->xoff, b->rq,
+                  b->tau_aw0, b->gas, b->user, b->xk, b->wk, b->KL, b->err, b->out_dev,
+                  b->tcblocks, b->kimg, b->F1, b->F2, b->mp[0], b->mp[1], b->ytmp};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete b;
+}
+
+template <typename X>
+int dev_upload(X** dst, const X* src, size_t n) {
+  if (cudaMalloc((void**)dst, sizeof(X) * std::max<size_t>(n, 1)) != cudaSuccess)
+    return set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cudaMalloc failed");
+  if (n && cudaMemcpy(*dst, src, sizeof(X) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return set_error(RSLB_ERR_CUDA, "rslb_bjorken_init: copy to device failed");
+  return RSLB_OK;
+}
+
+int bj_check_err(rslb_bjorken* b) {
+  int herr[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(herr, b->err, sizeof(herr), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_error(e, "rslb_bjorken: synchronising");
+  if (herr[0]) {
+    cudaMemsetAsync(b->err, 0, 2 * sizeof(int), b->stream);
+    cudaStreamSynchronize(b->stream);
+    const int user = (herr[1] >= 0 && herr[1] < b->nruns) ? b->user_of_sorted[herr[1]] : -1;
+    return set_error(RSLB_ERR_NONPHYSICAL, "rslb_bjorken: non-physical state in run %d", user);
+  }
+  return RSLB_OK;
+}
+
+// Runs per CTA block for a given Q: three copies of the block state within
+// ~200 KB of shared memory, a multiple of the register block RB when R >= RB.
+int runs_per_block(int Q, int QL, size_t es, int RB) {
+  const size_t budget = 200 * 1024;
+  const size_t per_run = 3 * es * (size_t)Q * QL;
+  int R = (int)(budget / per_run);
+  R = std::max(1, std::min(R, 64));
+  if (R >= RB) R = R / RB * RB;
+  return R;
+}
+
+size_t block_smem_bytes(int Q, int R, int QL, size_t es, int RB) {
+  const int RP = (R + RB - 1) / RB * RB;
+  const size_t state = 3 * es * (size_t)Q * RP * QL;
+  return ((state + 15) & ~size_t(15)) + sizeof(double) * 3 * RP;
+}
+
+}  // namespace
+
+extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* runs, int nruns,
+                                 const rslb_bjorken_opts* o, void* stream) {
+  clear_error();
+  if (!out || !runs || !o || nruns < 1)
+    return set_error(RSLB_ERR_ARG, "rslb_bjorken_init: NULL argument or nruns < 1");
+  *out = nullptr;
+  if (o->Q_L < 1 || o->Q_L > kBjMaxQL || (o->precision != RSLB_F32 && o->precision != RSLB_F64) ||
+      (o->kp_mode != RSLB_KP_SIMT && o->kp_mode != RSLB_KP_BF16X3 &&
+       o->kp_mode != RSLB_KP_TF32X3) ||
+      !(o->tau0 > 0.0) || !(o->dtau > 0.0) || !std::isfinite(o->dtau))
+    return set_error(RSLB_ERR_ARG, "rslb_bjorken_init: invalid options");
+  if (o->kp_mode == RSLB_KP_BF16X3)
+    return set_error(RSLB_ERR_UNSUPPORTED,
+                     "rslb_bjorken_init: RSLB_KP_BF16X3 is not available (use RSLB_KP_TF32X3)");
+  if (o->kp_mode == RSLB_KP_TF32X3 && (o->precision != RSLB_F32 || o->Q_L > 4))
+    return set_error(RSLB_ERR_UNSUPPORTED,
+                     "rslb_bjorken_init: RSLB_KP_TF32X3 needs RSLB_F32 and Q_L <= 4");
+  for (int r = 0; r < nruns; ++r) {
+    const rslb_bjorken_run& R = runs[r];
+    if (R.Q_xi < 2 || R.Q_xi > kBjMaxQ || (R.gas != RSLB_GAS_PARTON && R.gas != RSLB_GAS_IDEAL))
+      return set_error(RSLB_ERR_ARG, "rslb_bjorken_init: run %d: need 2 <= Q_xi <= %d and a "
+                       "known gas", r, kBjMaxQ);
+    // initial state: P = 1, T = 1, so tau_AW = tau_AW0 (both gas laws)
+    if (R.tau_AW0 > 0.0 && std::isfinite(R.tau_AW0) && o->dtau >= R.tau_AW0)
+      return set_error(RSLB_ERR_STIFF, "rslb_bjorken_init: run %d: dtau >= tau_AW0", r);
+  }
+  const size_t es = o->precision == RSLB_F64 ? sizeof(double) : sizeof(float);
+  rslb_bjorken* b = new rslb_bjorken();
+  b->nruns = nruns;
+  b->QL = o->Q_L;
+  b->precision = o->precision;
+  b->kp_mode = o->kp_mode;
+  b->tau0 = o->tau0;
+  b->dtau = o->dtau;
+  b->steps = 0;
+  b->stream = (cudaStream_t)stream;
+  b->state = b->kpool = nullptr;
+  b->npool = nullptr;
+  b->blocks = nullptr;
+  b->qtab = nullptr;
+  b->roff = b->xoff = nullptr;
+  b->rq = b->gas = b->user = b->err = nullptr;
+  b->tau_aw0 = b->xk = b->wk = b->KL = b->out_dev = nullptr;
+  b->tcblocks = nullptr;
+  b->ntc = 0;
+  b->tc_smem = 0;
+  b->kimg = nullptr;
+  b->F1 = b->F2 = nullptr;
+  b->mp[0] = b->mp[1] = nullptr;
+  b->mp_cur = 0;
+  b->ytmp = nullptr;
+  const int QL = o->Q_L;
+
+  // sort runs by Q (descending: the heaviest blocks start first), stable
+  std::vector<int> order(nruns);
+  for (int r = 0; r < nruns; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int c) { return runs[a].Q_xi > runs[c].Q_xi; });
+  b->user_of_sorted = order;
+  // distinct Q tables
+  std::vector<int> qvals;
+  for (int r : order)
+    if (qvals.empty() || qvals.back() != runs[r].Q_xi) qvals.push_back(runs[r].Q_xi);
+  std::vector<BjQTab> qtab(qvals.size());
+  std::vector<double> npool;
+  long long kp_total = 0;
+  for (size_t i = 0; i < qvals.size(); ++i) {
+    const int Q = qvals[i];
+    qtab[i].xi_off = (long long)npool.size();
+    qtab[i].kp_off = kp_total;
+    std::vector<double> x(Q), w(Q);
+    gauss_legendre_host(Q, x.data(), w.data());
+    npool.insert(npool.end(), x.begin(), x.end());
+    npool.insert(npool.end(), w.begin(), w.end());
+    kp_total += (long long)Q * Q;
+  }
+  // per-run tables (sorted order) and blocks
+  std::vector<long long> roff(nruns), xoff(nruns);
+  std::vector<int> rq(nruns), gasv(nruns), user(nruns);
+  std::vector<double> t0(nruns);
+  std::vector<BjBlock> blocks;
+  long long off = 0;
+  size_t qi = 0;
+  for (int s = 0; s < nruns; ++s) {
+    const int r = order[s];
+    while (qvals[qi] != runs[r].Q_xi) ++qi;
+    rq[s] = runs[r].Q_xi;
+    roff[s] = off;
+    off += (long long)QL * runs[r].Q_xi;
+    xoff[s] = qtab[qi].xi_off;
+    gasv[s] = runs[r].gas;
+    t0[s] = runs[r].tau_AW0;
+    user[s] = r;
+  }
+  b->total_state = off;
+  size_t max_smem = 0;
+  const int RB = (es == sizeof(double)) ? 4 : 8;
+  for (int s = 0; s < nruns;) {
+    const int Q = rq[s];
+    const int Rmax = runs_per_block(Q, QL, es, RB);
+    int n = 0;
+    while (s + n < nruns && rq[s + n] == Q && n < Rmax) ++n;
+    size_t qidx = 0;
+    while (qvals[qidx] != Q) ++qidx;
+    blocks.push_back(BjBlock{Q, s, n, (int)qidx});
+    max_smem = std::max(max_smem, block_smem_bytes(Q, n, QL, es, RB));
+    s += n;
+  }
+  b->nblocks = (int)blocks.size();
+  b->smem = max_smem;
+  // tensor-core work units: runs of equal Q in blocks of at most kTcMaxCols
+  // columns (two CTAs per SM), split evenly, times the M-tiles of K^P
+  std::vector<BjTcBlock> tcb;
+  std::vector<long long> img_off(qvals.size(), 0);
+  long long img_total = 0;
+  for (size_t i = 0; i < qvals.size(); ++i) {
+    img_off[i] = img_total;
+    img_total += (long long)qvals[i] * ((qvals[i] + 31) / 32) * 32;
+  }
+  if (o->kp_mode == RSLB_KP_TF32X3) {
+    const int rmax = std::max(1, kTcMaxCols / QL);
+    size_t tc_smem = 0;
+    for (int s = 0; s < nruns;) {
+      const int Q = rq[s];
+      int n = 0;
+      while (s + n < nruns && rq[s + n] == Q) ++n;
+      size_t qi = 0;
+      while (qvals[qi] != Q) ++qi;
+      const int nb = (n + rmax - 1) / rmax;
+      for (int k = 0, done = 0; k < nb; ++k) {
+        const int R = (n - done + (nb - k) - 1) / (nb - k);
+        BjTcBlock t{};
+        t.Q = Q;
+        t.first = s + done;
+        t.R = R;
+        t.nmt = (Q + 127) / 128;
+        t.nc = (R * QL + 15) / 16 * 16;
+        t.tmem_cols = 32;
+        while (t.tmem_cols < t.nc) t.tmem_cols *= 2;
+        t.soff = roff[s + done];
+        t.img = img_off[qi];
+        t.xoff = qtab[qi].xi_off;
+        for (int m = 0; m < t.nmt; ++m) {
+          t.mt = m;
+          tcb.push_back(t);
+        }
+        tc_smem = std::max(tc_smem, bj_tc_smem_bytes(t.nc, R));
+        done += R;
+      }
+      s += n;
+    }
+    b->ntc = (int)tcb.size();
+    b->tc_smem = tc_smem;
+  }
+  b->roff_h = roff;
+  b->rq_h = rq;
+  std::vector<double> xk(QL), wk(QL);
+  gauss_laguerre2_host(QL, xk.data(), wk.data());
+
+  int rc = RSLB_OK;
+  if (!rc) rc = dev_upload(&b->npool, npool.data(), npool.size());
+  if (!rc) rc = dev_upload(&b->qtab, qtab.data(), qtab.size());
+  if (!rc) rc = dev_upload(&b->blocks, blocks.data(), blocks.size());
+  if (!rc) rc = dev_upload(&b->roff, roff.data(), roff.size());
+  if (!rc) rc = dev_upload(&b->xoff, xoff.data(), xoff.size());
+  if (!rc) rc = dev_upload(&b->rq, rq.data(), rq.size());
+  if (!rc) rc = dev_upload(&b->gas, gasv.data(), gasv.size());
+  if (!rc) rc = dev_upload(&b->user, user.data(), user.size());
+  if (!rc) rc = dev_upload(&b->tau_aw0, t0.data(), t0.size());
+  if (!rc) rc = dev_upload(&b->xk, xk.data(), xk.size());
+  if (!rc) rc = dev_upload(&b->wk, wk.data(), wk.size());
+  if (!rc && cudaMalloc((void**)&b->KL, sizeof(double) * QL * QL) != cudaSuccess)
+    rc = set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cudaMalloc failed");
+  if (!rc && cudaMalloc(&b->state, es * (size_t)b->total_state) != cudaSuccess)
+    rc = set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cannot allocate the state");
+  if (!rc && cudaMalloc(&b->kpool, es * (size_t)kp_total) != cudaSuccess)
+    rc = set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cannot allocate K^P (%lld entries)",
+                   kp_total);
+  if (!rc && cudaMalloc((void**)&b->err, 2 * sizeof(int)) != cudaSuccess)
+    rc = set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cudaMalloc failed");
+  if (!rc && cudaMalloc((void**)&b->out_dev, sizeof(double) * RSLB_BJ_NOUT * nruns) != cudaSuccess)
+    rc = set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cudaMalloc failed");
+  if (!rc && o->kp_mode == RSLB_KP_TF32X3) {
+    rc = dev_upload(&b->tcblocks, tcb.data(), tcb.size());
+    const size_t sb = sizeof(float) * (size_t)b->total_state;
+    if (!rc && (cudaMalloc((void**)&b->kimg, sizeof(float) * (size_t)img_total) != cudaSuccess ||
+                cudaMalloc(&b->F1, sb) != cudaSuccess || cudaMalloc(&b->F2, sb) != cudaSuccess ||
+                cudaMalloc((void**)&b->ytmp, sb) != cudaSuccess ||
+                cudaMalloc((void**)&b->mp[0], sizeof(double) * 8 * nruns) != cudaSuccess ||
+                cudaMalloc((void**)&b->mp[1], sizeof(double) * 8 * nruns) != cudaSuccess))
+      rc = set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cannot allocate the tensor-core buffers");
+  }
+  if (rc) {
+    bj_free(b);
+    return rc;
+  }
+  cudaStream_t st = b->stream;
+  cudaMemsetAsync(b->err, 0, 2 * sizeof(int), st);
+  // K^P per distinct Q, K^L, initial state
+  for (size_t i = 0; i < qvals.size(); ++i) {
+    const int Q = qvals[i];
+    const int n = Q * Q;
+    if (b->precision == RSLB_F64)
+      bj_kp_kernel<double><<<(n + 255) / 256, 256, 0, st>>>(
+          Q, b->npool + qtab[i].xi_off, (double*)b->kpool + qtab[i].kp_off);
+    else
+      bj_kp_kernel<float><<<(n + 255) / 256, 256, 0, st>>>(
+          Q, b->npool + qtab[i].xi_off, (float*)b->kpool + qtab[i].kp_off);
+  }
+  if (o->kp_mode == RSLB_KP_TF32X3) {
+    cudaMemsetAsync(b->kimg, 0, sizeof(float) * (size_t)img_total, st);
+    for (size_t i = 0; i < qvals.size(); ++i)
+      bj_tc_image_launch(qvals[i], b->npool + qtab[i].xi_off, b->kimg + img_off[i], st);
+  }
+  bj_kl_kernel<<<1, QL * QL, 0, st>>>(QL, b->xk, b->wk, b->KL);
+  if (b->precision == RSLB_F64)
+    bj_init_kernel<double><<<nruns, 128, 0, st>>>(nruns, QL, b->rq, b->roff, b->xoff, b->npool,
+                                                   b->wk, (double*)b->state);
+  else
+    bj_init_kernel<float><<<nruns, 128, 0, st>>>(nruns, QL, b->rq, b->roff, b->xoff, b->npool,
+                                                  b->wk, (float*)b->state);
+  if (o->kp_mode == RSLB_KP_TF32X3)
+    bj_tc_moments_launch(nruns, QL, b->rq, b->roff, b->xk, (const float*)b->state,
+                         b->mp[b->mp_cur], st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    bj_free(b);
+    return cuda_error(e, "rslb_bjorken_init: set-up kernels");
+  }
+  if (o->kp_mode == RSLB_KP_TF32X3) {
+    e = bj_tc_set_attributes();
+    if (e != cudaSuccess) {
+      bj_free(b);
+      return cuda_error(e, "rslb_bjorken_init: shared-memory attribute");
+    }
+  }
+  const void* kfun = b->precision == RSLB_F64 ? (const void*)bj_step_kernel<double, 4>
+                                              : (const void*)bj_step_kernel<float, 8>;
+  e = cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (e != cudaSuccess) {
+    bj_free(b);
+    return cuda_error(e, "rslb_bjorken_init: shared-memory attribute");
+  }
+  *out = b;
+  return RSLB_OK;
+}
+
+extern "C" int rslb_bjorken_step(rslb_bjorken* b, int nsteps) {
+  clear_error();
+  if (!b || nsteps < 0) return set_error(RSLB_ERR_ARG, "rslb_bjorken_step: bad arguments");
+  if (nsteps == 0) return RSLB_OK;
+  const double tau_start = b->tau0 + b->steps * b->dtau;
+  cudaError_t e;
+  if (b->kp_mode == RSLB_KP_TF32X3) {
+    float* F[3] = {(float*)b->state, (float*)b->F1, (float*)b->F2};
+    const double cst[3] = {0.0, 1.0, 0.5};
+    e = cudaSuccess;
+    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      const double tn = tau_start + n * b->dtau;
+      for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+        BjTcArgs a{};
+        a.blocks = b->tcblocks;
+        a.kimg = b->kimg;
+        a.npool = b->npool;
+        a.tau_aw0 = b->tau_aw0;
+        a.gas = b->gas;
+        a.xk = b->xk;
+        a.wk = b->wk;
+        a.KL = b->KL;
+        a.QL = b->QL;
+        a.stage = stage;
+        a.Fin = F[stage];
+        a.Fn = F[0];
+        a.Fout = F[(stage + 1) % 3];
+        a.mp_in = b->mp[b->mp_cur];
+        a.mp_out = b->mp[1 - b->mp_cur];
+        a.dout = nullptr;
+        a.tau = tn + cst[stage] * b->dtau;
+        a.dtau = b->dtau;
+        a.err = b->err;
+        e = bj_tc_stage_launch(a, b->ntc, b->tc_smem, b->stream);
+        b->mp_cur = 1 - b->mp_cur;
+      }
+    }
+    if (e != cudaSuccess) return cuda_error(e, "rslb_bjorken_step: launch");
+    b->steps += nsteps;
+    return RSLB_OK;
+  }
+  if (b->precision == RSLB_F64) {
+    BjArgs<double> a{b->blocks, b->qtab, (const double*)b->kpool, b->npool, b->roff,
+                     b->tau_aw0, b->gas, (double*)b->state, b->xk, b->wk, b->KL, b->QL,
+                     nsteps, tau_start, b->dtau, b->err};
+    bj_step_kernel<double, 4><<<b->nblocks, kBjThreads, b->smem, b->stream>>>(a, 0);
+  } else {
+    BjArgs<float> a{b->blocks, b->qtab, (const float*)b->kpool, b->npool, b->roff,
+                    b->tau_aw0, b->gas, (float*)b->state, b->xk, b->wk, b->KL, b->QL,
+                    nsteps, tau_start, b->dtau, b->err};
+    bj_step_kernel<float, 8><<<b->nblocks, kBjThreads, b->smem, b->stream>>>(a, 0);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "rslb_bjorken_step: launch");
+  b->steps += nsteps;
+  return RSLB_OK;
+}
+
+extern "C" int rslb_bjorken_read(rslb_bjorken* b, double* out, int out_on_device) {
+  clear_error();
+  if (!b || !out) return set_error(RSLB_ERR_ARG, "rslb_bjorken_read: NULL argument");
+  const double tau = b->tau0 + b->steps * b->dtau;
+  const int warps = 8;
+  const int grid = (b->nruns + warps - 1) / warps;
+  if (b->precision == RSLB_F64)
+    bj_read_kernel<double><<<grid, 32 * warps, 0, b->stream>>>(
+        b->nruns, b->QL, b->rq, b->roff, b->xoff, b->npool, b->gas, b->user, b->xk,
+        (const double*)b->state, tau, b->out_dev, b->err);
+  else
+    bj_read_kernel<float><<<grid, 32 * warps, 0, b->stream>>>(
+        b->nruns, b->QL, b->rq, b->roff, b->xoff, b->npool, b->gas, b->user, b->xk,
+        (const float*)b->state, tau, b->out_dev, b->err);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, b->out_dev, sizeof(double) * RSLB_BJ_NOUT * b->nruns,
+                        out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        b->stream);
+  if (e != cudaSuccess) return cuda_error(e, "rslb_bjorken_read");
+  return bj_check_err(b);
+}
+
+extern "C" int rslb_bjorken_get_state(rslb_bjorken* b, void* f) {
+  clear_error();
+  if (!b || !f) return set_error(RSLB_ERR_ARG, "rslb_bjorken_get_state: NULL argument");
+  const size_t es = b->precision == RSLB_F64 ? sizeof(double) : sizeof(float);
+  std::vector<unsigned char> tmp(es * (size_t)b->total_state);
+  cudaError_t e = cudaMemcpyAsync(tmp.data(), b->state, tmp.size(), cudaMemcpyDeviceToHost,
+                                  b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_error(e, "rslb_bjorken_get_state");
+  // sorted -> caller order
+  std::vector<long long> uoff(b->nruns + 1, 0);
+  std::vector<int> uq(b->nruns);
+  for (int s = 0; s < b->nruns; ++s) uq[b->user_of_sorted[s]] = b->rq_h[s];
+  for (int r = 0; r < b->nruns; ++r) uoff[r + 1] = uoff[r] + (long long)b->QL * uq[r];
+  for (int s = 0; s < b->nruns; ++s) {
+    const int r = b->user_of_sorted[s];
+    std::memcpy((unsigned char*)f + es * uoff[r], tmp.data() + es * b->roff_h[s],
+                es * (size_t)b->QL * b->rq_h[s]);
+  }
+  return bj_check_err(b);
+}
+
+extern "C" int rslb_bjorken_set_state(rslb_bjorken* b, const void* f) {
+  clear_error();
+  if (!b || !f) return set_error(RSLB_ERR_ARG, "rslb_bjorken_set_state: NULL argument");
+  const size_t es = b->precision == RSLB_F64 ? sizeof(double) : sizeof(float);
+  std::vector<unsigned char> tmp(es * (size_t)b->total_state);
+  std::vector<long long> uoff(b->nruns + 1, 0);
+  std::vector<int> uq(b->nruns);
+  for (int s = 0; s < b->nruns; ++s) uq[b->user_of_sorted[s]] = b->rq_h[s];
+  for (int r = 0; r < b->nruns; ++r) uoff[r + 1] = uoff[r] + (long long)b->QL * uq[r];
+  for (int s = 0; s < b->nruns; ++s) {
+    const int r = b->user_of_sorted[s];
+    std::memcpy(tmp.data() + es * b->roff_h[s], (const unsigned char*)f + es * uoff[r],
+                es * (size_t)b->QL * b->rq_h[s]);
+  }
+  cudaError_t e = cudaMemcpyAsync(b->state, tmp.data(), tmp.size(), cudaMemcpyHostToDevice,
+                                  b->stream);
+  if (e == cudaSuccess && b->kp_mode == RSLB_KP_TF32X3)
+    e = bj_tc_moments_launch(b->nruns, b->QL, b->rq, b->roff, b->xk, (const float*)b->state,
+                             b->mp[b->mp_cur], b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_error(e, "rslb_bjorken_set_state");
+  return RSLB_OK;
+}
+
+extern "C" int rslb_bjorken_kp_apply(rslb_bjorken* b, void* y) {
+  clear_error();
+  if (!b || !y) return set_error(RSLB_ERR_ARG, "rslb_bjorken_kp_apply: NULL argument");
+  if (b->kp_mode != RSLB_KP_TF32X3)
+    return set_error(RSLB_ERR_UNSUPPORTED, "rslb_bjorken_kp_apply: needs RSLB_KP_TF32X3");
+  BjTcArgs a{};
+  a.blocks = b->tcblocks;
+  a.kimg = b->kimg;
+  a.npool = b->npool;
+  a.tau_aw0 = b->tau_aw0;
+  a.gas = b->gas;
+  a.xk = b->xk;
+  a.wk = b->wk;
+  a.KL = b->KL;
+  a.QL = b->QL;
+  a.stage = -1;
+  a.Fin = (const float*)b->state;
+  a.Fn = (const float*)b->state;
+  a.Fout = nullptr;
+  a.mp_in = b->mp[b->mp_cur];
+  a.mp_out = nullptr;
+  a.dout = b->ytmp;
+  a.tau = 1.0;
+  a.dtau = b->dtau;
+  a.err = b->err;
+  cudaError_t e = bj_tc_stage_launch(a, b->ntc, b->tc_smem, b->stream);
+  std::vector<float> tmp((size_t)b->total_state);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tmp.data(), b->ytmp, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_error(e, "rslb_bjorken_kp_apply");
+  std::vector<long long> uoff(b->nruns + 1, 0);
+  std::vector<int> uq(b->nruns);
+  for (int s = 0; s < b->nruns; ++s) uq[b->user_of_sorted[s]] = b->rq_h[s];
+  for (int r = 0; r < b->nruns; ++r) uoff[r + 1] = uoff[r] + (long long)b->QL * uq[r];
+  for (int s = 0; s < b->nruns; ++s) {
+    const int r = b->user_of_sorted[s];
+    std::memcpy((float*)y + uoff[r], tmp.data() + b->roff_h[s],
+                sizeof(float) * (size_t)b->QL * b->rq_h[s]);
+  }
+  return bj_check_err(b);
+}
+
+extern "C" void rslb_bjorken_destroy(rslb_bjorken* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  bj_free(b);
+}

@@ -1,0 +1,548 @@
+// bjorken_tc.cu -- the Bjorken K^P contraction on the 5th-generation tensor
+// cores (tcgen05, kind::tf32, FP32 accumulators in tensor memory).
+//
+// One RK stage (Eq. rk3 with L_Bjorken, Eq. L_Bjorken) of a block of runs
+// that share Q_xi is split over the M-tiles of K^P: the CTA of M-tile mt
+// computes, for rows j in [128 mt, 128 mt + 128) and every column c = (run, k)
+// of the block,
+//     D[j][c] = sum_j' K^P[j][j'] f_c[j']                          (Eq. K_leg_disc)
+// as an M = 128, N = nc, K = 8 MMA chain.  FP32 operands are split
+// x = hi + lo with hi = tf32(x) (round to nearest) and lo = x - hi (exact),
+// and D = Khi fhi + Khi flo + Klo fhi ("3xTF32"): the dropped Klo flo term
+// and the TF32 truncation of the lo parts leave ~2^-20 relative error per
+// product, FP32-level for this contraction.
+//
+// Data movement: K^P is stored once per distinct Q as an FP32 image whose
+// 128-row x 32-column tiles are already in the 128-byte-swizzled K-major
+// order the MMA descriptors expect; a tile is brought in by one bulk copy
+// (cp.async.bulk, completion on an mbarrier) and split into hi/lo in place.
+// The state f of the block is read from HBM/L2 per 32-row K-block, split and
+// stored swizzled by the threads.  Two pipeline stages: the bulk copy of
+// K-block it+1 and the thread work of K-block it+1 overlap the MMAs of it.
+// The epilogue reads its row of D from TMEM (tcgen05.ld), adds the K^L and
+// -f/tau terms and the Anderson-Witting collision with the equilibrium of
+// the stage state, applies the RK combination and writes f and the run's
+// moment partials (N, E) for the next stage.
+//
+// Every mbarrier wait is bounded; on time-out the CTA records an error,
+// waits (bounded) for what it issued, frees its tensor memory and returns.
+#include <cstdint>
+
+#include "../../include/rslb.h"
+#include "bjorken.cuh"
+
+namespace rslb {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr uint32_t kATile = 128 * 128;  // bytes: 128 rows x 32 FP32
+constexpr int kSpinLimit = 1 << 22;
+constexpr int kErrTimeout = 97;
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kSpinLimit; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// 128B-swizzled K-major smem descriptor (tile base 1024-byte aligned; the
+// start address may be advanced by 32 B per K step inside the swizzle atom).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout): 16 B
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Byte offset of element (row, col), col < 32, in a 128B-swizzled K-major
+// FP32 tile: 16-byte chunk index XOR (row mod 8).
+__host__ __device__ __forceinline__ uint32_t swz(int row, int col) {
+  return (uint32_t)(row * 128 + ((((col >> 2) ^ row) & 7) << 4) + ((col & 3) << 2));
+}
+
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ void tc_report(int* err, int code, int run) {
+  if (atomicCAS(err, 0, code) == 0) err[1] = run;
+}
+
+// ---------------------------------------------------------------------------
+// The stage kernel
+// ---------------------------------------------------------------------------
+template <int QL>
+__global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  const BjTcBlock blk = a.blocks[blockIdx.x];
+  const int Q = blk.Q, R = blk.R, NC = blk.nc, mt = blk.mt;
+  const int ncv = R * QL;
+  const int nkb = (Q + 31) / 32;
+  const int rows = min(128, Q - 128 * mt);
+  const uint32_t btile = (uint32_t)NC * 128u;
+  const uint32_t sstride = 2 * kATile + 2 * btile;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  auto Ahi = [&](int s) { return base + s * sstride; };
+  auto Alo = [&](int s) { return base + s * sstride + kATile; };
+  auto Bhi = [&](int s) { return base + s * sstride + 2 * kATile; };
+  auto Blo = [&](int s) { return base + s * sstride + 2 * kATile + btile; };
+  unsigned char* tail = base + 2 * sstride;
+  uint64_t* full = reinterpret_cast<uint64_t*>(tail);  // [2]
+  uint64_t* done = full + 2;                           // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 2);
+  float* rs = reinterpret_cast<float*>(tail + 64);  // rate[R] | neq4[R] | omt[R]
+  float* mp = rs + 3 * R;                           // [4 warps][R][2]
+
+  // zero the A buffers (rows past the end of K^P stay zero), set up barriers
+  {
+    float4* z = reinterpret_cast<float4*>(base);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < 2; ++s)
+      for (int i = tid; i < (int)(2 * kATile / 16); i += kTcThreads)
+        z[s * (sstride / 16) + i] = zero;
+  }
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&done[0], 1);
+    mbar_init(&done[1], 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_slot)),
+                 "r"(blk.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const float* Asrc = a.kimg + blk.img + (size_t)mt * 128 * nkb * 32;
+  const uint32_t abytes = (uint32_t)rows * 128u;
+  const uint32_t idesc = idesc_tf32(NC);
+  // issued-but-unconfirmed work of thread 0 (for the abort path)
+  int last_copy = -1, last_commit = -1;
+  if (tid == 0) {
+    mbar_expect_tx(&full[0], abytes);
+    bulk_g2s(Ahi(0), Asrc, abytes, &full[0]);
+    last_copy = 0;
+  }
+
+  // per-run equilibrium of the stage state from the moment partials
+  const bool rk = a.stage >= 0;
+  if (rk) {
+    for (int r = tid; r < R; r += kTcThreads) {
+      const int gr = blk.first + r;
+      double N = 0.0, E = 0.0;
+      for (int m = 0; m < blk.nmt; ++m) {
+        N += a.mp_in[((size_t)gr * 4 + m) * 2];
+        E += a.mp_in[((size_t)gr * 4 + m) * 2 + 1];
+      }
+      double rate = 0.0, neq4 = 0.0, omt = 0.0;
+      const double P = E / 3.0;
+      const double t0 = a.tau_aw0[gr];
+      const bool coll = t0 > 0.0 && isfinite(t0);
+      if (!(P > 0.0) || !isfinite(P) || (a.gas[gr] == RSLB_GAS_IDEAL && !(N > 0.0))) {
+        if (mt == 0) tc_report(a.err, RSLB_ERR_NONPHYSICAL, gr);
+      } else if (coll) {
+        double T_, n_eq, tau_aw;
+        if (a.gas[gr] == RSLB_GAS_PARTON) {
+          T_ = sqrt(sqrt(P));
+          n_eq = P / T_;
+          tau_aw = t0 / T_;
+        } else {
+          T_ = P / N;
+          n_eq = N;
+          tau_aw = t0 / T_ * (1.0 - 0.25 * log(N / (T_ * T_ * T_)));
+        }
+        rate = 1.0 / tau_aw;
+        neq4 = 0.25 * n_eq;
+        omt = 1.0 - T_;
+      }
+      rs[r] = float(rate);
+      rs[R + r] = float(neq4);
+      rs[2 * R + r] = float(omt);
+    }
+  }
+
+  // ---- main loop over K-blocks of 32 rows j' ----
+  const float* Fblk = a.Fin + blk.soff;
+  bool aborted = false;
+  for (int it = 0; it < nkb; ++it) {
+    const int s = it & 1;
+    const uint32_t par = (uint32_t)(it >> 1) & 1u;
+    const int jj = it * 32 + lane;
+    // state rows c = warp, warp + 4, ...: 8 loads in flight per thread
+    for (int c0 = warp; c0 < NC; c0 += 32) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = c0 + 4 * u;
+        v[u] = (c < ncv && jj < Q) ? Fblk[(size_t)c * Q + jj] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = c0 + 4 * u;
+        if (c < NC) {
+          const float hi = tf32_rn(v[u]);
+          const uint32_t o = swz(c, lane);
+          *reinterpret_cast<float*>(Bhi(s) + o) = hi;
+          *reinterpret_cast<float*>(Blo(s) + o) = v[u] - hi;
+        }
+      }
+    }
+    // K^P tile of this K-block: wait for the bulk copy, split in place
+    const int copy_lost = !mbar_wait(&full[s], par);
+    {
+      float4* ah = reinterpret_cast<float4*>(Ahi(s));
+      float4* al = reinterpret_cast<float4*>(Alo(s));
+      for (int i = tid; i < rows * 8; i += kTcThreads) {
+        const float4 x = ah[i];
+        const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
+        ah[i] = h;
+        al[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+    }
+    fence_proxy_async();
+    if (__syncthreads_or(copy_lost)) {
+      if (tid == 0) tc_report(a.err, kErrTimeout, blk.first);
+      aborted = true;
+      break;
+    }
+    int mma_lost = 0;
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint64_t ah = sdesc(su32(Ahi(s)) + 32u * ks), al = sdesc(su32(Alo(s)) + 32u * ks);
+        const uint64_t bh = sdesc(su32(Bhi(s)) + 32u * ks), bl = sdesc(su32(Blo(s)) + 32u * ks);
+        mma_tf32(tmem, ah, bh, idesc, (it > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, ah, bl, idesc, 1u);
+        mma_tf32(tmem, al, bh, idesc, 1u);
+      }
+      mma_commit(&done[s]);
+      last_commit = it;
+      if (it + 1 < nkb) {
+        // buffer (it+1)&1 was last read by the MMAs of it-1
+        bool ok = true;
+        if (it >= 1) ok = mbar_wait(&done[(it - 1) & 1], (uint32_t)((it - 1) >> 1) & 1u);
+        if (ok) {
+          mbar_expect_tx(&full[(it + 1) & 1], abytes);
+          bulk_g2s(Ahi((it + 1) & 1), Asrc + (size_t)(it + 1) * rows * 32, abytes,
+                   &full[(it + 1) & 1]);
+          last_copy = it + 1;
+        } else {
+          tc_report(a.err, kErrTimeout, blk.first);
+          mma_lost = 1;
+        }
+      }
+    }
+    if (__syncthreads_or(mma_lost)) {
+      aborted = true;
+      break;
+    }
+  }
+
+  // all MMAs done (commits complete in issue order); the outcome is made
+  // uniform across the CTA before anyone branches on it
+  int lost = aborted ? 1 : !mbar_wait(&done[(nkb - 1) & 1], (uint32_t)((nkb - 1) >> 1) & 1u);
+  if (__syncthreads_or(lost)) {
+    if (tid == 0 && !aborted) tc_report(a.err, kErrTimeout, blk.first);
+    // bounded wait for what thread 0 issued, then release tensor memory
+    if (tid == 0) {
+      if (last_commit >= 0) mbar_wait(&done[last_commit & 1], (uint32_t)(last_commit >> 1) & 1u);
+      if (last_copy > last_commit) mbar_wait(&full[last_copy & 1], (uint32_t)(last_copy >> 1) & 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(blk.tmem_cols)
+                   : "memory");
+    }
+    return;
+  }
+  tc_fence_after();
+
+  // ---- epilogue: row j of D per thread ----
+  const int j = 128 * mt + 32 * warp + lane;
+  const bool rowok = j < Q;
+  float xi2 = 0.f, wj = 0.f;
+  if (rowok) {
+    const double x = a.npool[blk.xoff + j];
+    xi2 = float(x * x);
+    wj = float(a.npool[blk.xoff + Q + j]);
+  }
+  float KL[QL * QL], xk[QL], wk[QL], l1[QL];
+#pragma unroll
+  for (int k = 0; k < QL; ++k) {
+    xk[k] = float(a.xk[k]);
+    wk[k] = float(a.wk[k]);
+    l1[k] = float(3.0 - a.xk[k]);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) KL[k * QL + q] = float(a.KL[k * QL + q]);
+  }
+  const float itau = float(1.0 / a.tau), dt = float(a.dtau);
+  const float ca = a.stage == 1 ? 0.75f : 1.f / 3.f, cb = a.stage == 1 ? 0.25f : 2.f / 3.f;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+  const float* Fin = a.Fin + blk.soff;
+  const float* Fn = a.Fn + blk.soff;
+  float* Fout = a.Fout + blk.soff;
+  for (int rb = 0; rb < R; rb += 16) {
+    const int c0 = rb * QL;
+    uint32_t d[16 * QL];
+#pragma unroll
+    for (int p = 0; p < QL; ++p)
+      if (c0 + 16 * p < NC) tmem_ld16(trow + (uint32_t)(c0 + 16 * p), d + 16 * p);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int r = rb + i;
+      float on = 0.f, oe = 0.f;
+      if (r < R && rowok) {
+        float fk[QL];
+#pragma unroll
+        for (int k = 0; k < QL; ++k) fk[k] = Fin[(size_t)(r * QL + k) * Q + j];
+        if (!rk) {
+#pragma unroll
+          for (int k = 0; k < QL; ++k)
+            a.dout[blk.soff + (size_t)(r * QL + k) * Q + j] = __uint_as_float(d[i * QL + k]);
+        } else {
+          const float rate = rs[r], neq4 = rs[R + r], omt = rs[2 * R + r];
+#pragma unroll
+          for (int k = 0; k < QL; ++k) {
+            float klf = 0.f;
+#pragma unroll
+            for (int q = 0; q < QL; ++q) klf += KL[k * QL + q] * fk[q];
+            const float feq = neq4 * (wj * wk[k]) * (1.f + l1[k] * omt);
+            const float L = (-fk[k] + xi2 * klf + __uint_as_float(d[i * QL + k])) * itau -
+                            (fk[k] - feq) * rate;
+            const float v = fk[k] + dt * L;
+            const size_t o = (size_t)(r * QL + k) * Q + j;
+            float out = v;
+            if (a.stage == 1) out = ca * Fn[o] + cb * v;
+            else if (a.stage == 2) out = Fn[o] * ca + cb * v;
+            Fout[o] = out;
+            on += out;
+            oe += xk[k] * out;
+          }
+        }
+      }
+      if (rk) {
+        on = warp_sum_f(on);
+        oe = warp_sum_f(oe);
+        if (lane == 0 && r < R) {
+          mp[(warp * R + r) * 2] = on;
+          mp[(warp * R + r) * 2 + 1] = oe;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (rk) {
+    for (int r = tid; r < R; r += kTcThreads) {
+      double N = 0.0, E = 0.0;
+      for (int w = 0; w < 4; ++w) {
+        N += (double)mp[(w * R + r) * 2];
+        E += (double)mp[(w * R + r) * 2 + 1];
+      }
+      const int gr = blk.first + r;
+      a.mp_out[((size_t)gr * 4 + mt) * 2] = N;
+      a.mp_out[((size_t)gr * 4 + mt) * 2 + 1] = E;
+    }
+  }
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(blk.tmem_cols)
+                 : "memory");
+  }
+}
+
+// K^P image of one Q: tile (mt, kb) = rows j in M-tile mt (rows(mt) of them)
+// x columns j' = 32 kb .. 32 kb + 31, swizzled, stored at
+// img + (mt * 128 * nkb + kb * rows(mt)) * 32 floats.  Columns j' >= Q stay
+// zero (the buffer is cleared first).
+__global__ void bj_tc_image_kernel(int Q, const double* __restrict__ xw, float* img) {
+  const int nkb = (Q + 31) / 32;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Q * Q) return;
+  const int j = idx / Q, jp = idx - j * Q;
+  const int mt = j >> 7, row = j & 127, kb = jp >> 5, col = jp & 31;
+  const int rows = min(128, Q - 128 * mt);
+  float* tile = img + ((size_t)mt * 128 * nkb + (size_t)kb * rows) * 32;
+  tile[swz(row, col) >> 2] = float(kp_entry(Q, xw, j, jp));
+}
+
+// Moments (N, E) of each run into partial slot 0 (slots 1-3 cleared).
+__global__ void bj_tc_moments_kernel(int nruns, int QL, const int* __restrict__ rq,
+                                     const long long* __restrict__ roff,
+                                     const double* __restrict__ xk, const float* __restrict__ f,
+                                     double* mp) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= nruns) return;
+  const int Q = rq[r];
+  double N = 0.0, E = 0.0;
+  for (int v = lane; v < Q * QL; v += 32) {
+    const double fv = (double)f[roff[r] + v];
+    N += fv;
+    E += fv * xk[v / Q];
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    N += __shfl_xor_sync(0xffffffffu, N, o);
+    E += __shfl_xor_sync(0xffffffffu, E, o);
+  }
+  if (lane < 8) mp[(size_t)r * 8 + lane] = lane == 0 ? N : (lane == 1 ? E : 0.0);
+}
+
+}  // namespace
+
+size_t bj_tc_smem_bytes(int nc, int R) {
+  return 1024 + 2 * (2 * (size_t)kATile + 2 * (size_t)nc * 128) + 64 + sizeof(float) * 11 * (size_t)R;
+}
+
+cudaError_t bj_tc_set_attributes() {
+  const void* fns[] = {(const void*)bj_tc_stage_kernel<1>, (const void*)bj_tc_stage_kernel<2>,
+                       (const void*)bj_tc_stage_kernel<3>, (const void*)bj_tc_stage_kernel<4>};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t bj_tc_stage_launch(const BjTcArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+  switch (a.QL) {
+    case 1: bj_tc_stage_kernel<1><<<nblocks, kTcThreads, smem, st>>>(a); break;
+    case 2: bj_tc_stage_kernel<2><<<nblocks, kTcThreads, smem, st>>>(a); break;
+    case 3: bj_tc_stage_kernel<3><<<nblocks, kTcThreads, smem, st>>>(a); break;
+    case 4: bj_tc_stage_kernel<4><<<nblocks, kTcThreads, smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t bj_tc_image_launch(int Q, const double* xw, float* img, cudaStream_t st) {
+  const int n = Q * Q;
+  bj_tc_image_kernel<<<(n + 255) / 256, 256, 0, st>>>(Q, xw, img);
+  return cudaGetLastError();
+}
+
+cudaError_t bj_tc_moments_launch(int nruns, int QL, const int* rq, const long long* roff,
+                                 const double* xk, const float* state, double* mp,
+                                 cudaStream_t st) {
+  bj_tc_moments_kernel<<<(nruns + 7) / 8, 256, 0, st>>>(nruns, QL, rq, roff, xk, state, mp);
+  return cudaGetLastError();
+}
+
+}  // namespace rslb

@@ -1,5 +1,6 @@
 // host.cu -- C ABI of the R-SLB library (include/rslb.h): argument checks,
 // FP64 quadrature generation, velocity tables, device buffers and launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -218,7 +219,13 @@ struct rslb_handle {
   double* d_fields;
   double t;
   long long steps;
+  // CUDA graph of kGraphSteps steps (3 stage launches each), captured on the
+  // handle's stream the first time rslb_step is asked for that many steps
+  cudaGraphExec_t graph;
+  bool graph_failed;
 };
+
+static constexpr int kGraphSteps = 8;
 
 namespace {
 
@@ -251,6 +258,7 @@ SodTablesF64 tables64_of(const rslb_handle* h) {
 
 void free_handle(rslb_handle* h) {
   if (!h) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
   void* ptrs[] = {h->F[0], h->F[1], h->F[2], h->t_mw, h->t_xi, h->t_wp, h->t_L1k, h->t_gL,
                   h->t_gR, h->t_kidx, h->t_rowv, h->t_gl_t, h->t_gl_w, h->d_xi, h->d_p, h->d_wp,
                   h->d_L1k, h->d_err, h->d_fields};
@@ -332,15 +340,19 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
   if (ce != cudaSuccess) return cuda_error(ce, "cudaGetDevice");
   int max_smem = 0;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  ce = sod_set_attributes();
+  if (ce != cudaSuccess) return cuda_error(ce, "rslb_init: kernel attributes");
   const bool fp64 = c.precision == RSLB_F64;
   SodLaunch L = sod_pick_launch(fp64, V, QL, nm, max_smem);
   if (c.tile_cells != 0) {
     // explicit tile width (tuning): must be one the kernels are built for
     const bool okB = fp64 ? (c.tile_cells == 16 || c.tile_cells == 8)
-                          : (c.tile_cells == 32 || c.tile_cells == 16);
+                          : (c.tile_cells == 28 || c.tile_cells == 32 || c.tile_cells == 16);
     if (!okB)
       return set_error(RSLB_ERR_ARG, "rslb_init: tile_cells must be 0 or one of %s",
-                       fp64 ? "16, 8" : "32, 16");
+                       fp64 ? "16, 8" : "28, 32, 16");
+    if (c.tile_cells == 28 && (V < 128 || nm > 8))
+      return set_error(RSLB_ERR_ARG, "rslb_init: tile_cells = 28 needs V >= 128 and N_Omega <= 7");
     L.B = c.tile_cells;
   }
   if (L.B == 0)
@@ -544,10 +556,44 @@ static cudaError_t enqueue_steps(rslb_handle* h, int nsteps) {
   return cudaSuccess;
 }
 
+// Capture kGraphSteps steps into an executable graph (non-default streams only:
+// the legacy default stream cannot be captured).
+static cudaError_t build_graph(rslb_handle* h) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le =
+      h->fp64 ? enqueue_steps<double>(h, kGraphSteps) : enqueue_steps<float>(h, kGraphSteps);
+  e = cudaStreamEndCapture(h->stream, &g);
+  if (le != cudaSuccess) e = le;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e;
+}
+
 extern "C" int rslb_step(rslb_handle* h, int nsteps) {
   clear_error();
   if (!h || nsteps < 0) return set_error(RSLB_ERR_ARG, "rslb_step: bad handle or nsteps");
-  cudaError_t e = h->fp64 ? enqueue_steps<double>(h, nsteps) : enqueue_steps<float>(h, nsteps);
+  cudaError_t e = cudaSuccess;
+  int rest = nsteps;
+  if (h->stream != nullptr && nsteps >= kGraphSteps && !h->graph_failed) {
+    if (!h->graph) {
+      e = build_graph(h);
+      if (e != cudaSuccess) {
+        // fall back to plain launches (e.g. the caller's stream is being captured)
+        h->graph = nullptr;
+        h->graph_failed = true;
+        cudaGetLastError();
+        e = cudaSuccess;
+      }
+    }
+    while (h->graph && rest >= kGraphSteps && e == cudaSuccess) {
+      e = cudaGraphLaunch(h->graph, h->stream);
+      rest -= kGraphSteps;
+    }
+  }
+  if (e == cudaSuccess && rest > 0)
+    e = h->fp64 ? enqueue_steps<double>(h, rest) : enqueue_steps<float>(h, rest);
   if (e != cudaSuccess) return cuda_error(e, "rslb_step: launch");
   h->steps += nsteps;
   h->t = h->steps * h->cfg.dt;
@@ -600,6 +646,14 @@ extern "C" int rslb_set_state(rslb_handle* h, const void* f, int on_device) {
   return RSLB_OK;
 }
 
+extern "C" int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* threads) {
+  clear_error();
+  if (!h) return set_error(RSLB_ERR_ARG, "rslb_launch_info: NULL handle");
+  if (tile_cells) *tile_cells = h->launch.B;
+  if (threads) *threads = h->launch.B == 28 ? 224 : 320;
+  return RSLB_OK;
+}
+
 extern "C" int rslb_time(const rslb_handle* h, double* t, long long* steps) {
   clear_error();
   if (!h) return set_error(RSLB_ERR_ARG, "rslb_time: NULL handle");
@@ -612,4 +666,350 @@ extern "C" void rslb_destroy(rslb_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   free_handle(h);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of shock tubes
+// ---------------------------------------------------------------------------
+struct SodClass {
+  int V, nm, B, ctas_per_sm;
+  size_t smem;
+  void* runs_dev;  // SodRunDesc<T>[nr]
+  SodTask* tasks_dev;
+  int ntasks;
+};
+
+struct rslb_sod_batch {
+  int nruns;
+  bool fp64;
+  cudaStream_t stream;
+  std::vector<rslb_handle*> h;       // per run, caller order
+  std::vector<long long> nsteps;     // per run
+  std::vector<SodClass> cls;
+  long long* step_dev;
+  int* err;
+  long long steps_done, max_steps;
+  double total_cv;
+  int nsm;
+  cudaGraphExec_t graph;
+  bool graph_failed;
+};
+
+namespace {
+
+__global__ void batch_step_increment(long long* step) { *step += 1; }
+
+void batch_free(rslb_sod_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto& c : b->cls) {
+    if (c.runs_dev) cudaFree(c.runs_dev);
+    if (c.tasks_dev) cudaFree(c.tasks_dev);
+  }
+  if (b->step_dev) cudaFree(b->step_dev);
+  if (b->err) cudaFree(b->err);
+  for (rslb_handle* x : b->h) free_handle(x);
+  delete b;
+}
+
+template <typename T>
+cudaError_t batch_enqueue(rslb_sod_batch* b, int nsteps) {
+  for (int n = 0; n < nsteps; ++n) {
+    for (int stage = 0; stage < 3; ++stage)
+      for (const SodClass& c : b->cls) {
+        cudaError_t e = sod_batch_stage_launch<T>(
+            c.B, c.smem, c.ctas_per_sm * b->nsm, (const SodRunDesc<T>*)c.runs_dev, c.tasks_dev,
+            c.ntasks, b->step_dev, stage, b->err, c.V, b->stream);
+        if (e != cudaSuccess) return e;
+      }
+    batch_step_increment<<<1, 1, 0, b->stream>>>(b->step_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+int batch_build_classes(rslb_sod_batch* b, int autotune) {
+  // runs grouped by (V, nm); each group's runs sorted by decreasing step count
+  std::vector<int> order(b->nruns);
+  for (int r = 0; r < b->nruns; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (b->h[x]->V != b->h[y]->V) return b->h[x]->V < b->h[y]->V;
+    if (b->h[x]->nm != b->h[y]->nm) return b->h[x]->nm < b->h[y]->nm;
+    return b->nsteps[x] > b->nsteps[y];
+  });
+  int dev = 0, max_smem = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int QL = b->h[0]->cfg.Q_L;
+  for (size_t i = 0; i < order.size();) {
+    const int V = b->h[order[i]]->V, nm = b->h[order[i]]->nm;
+    size_t j = i;
+    while (j < order.size() && b->h[order[j]]->V == V && b->h[order[j]]->nm == nm) ++j;
+    SodClass c{};
+    c.V = V;
+    c.nm = nm;
+    const SodLaunch L = sod_pick_launch(b->fp64, V, QL, nm, max_smem);
+    if (L.B == 0)
+      return set_error(RSLB_ERR_UNSUPPORTED, "rslb_sod_batch_init: V = %d does not fit a tile", V);
+    c.B = L.B;
+    std::vector<SodRunDesc<T>> rd;
+    std::vector<SodTask> tasks;
+    for (size_t q = i; q < j; ++q) {
+      rslb_handle* hh = b->h[order[q]];
+      SodRunDesc<T> d;
+      d.g = hh->geom;
+      d.tb = tables_of<T>(hh);
+      d.rowv = hh->t_rowv;
+      d.nneg = hh->nneg;
+      d.F0 = (T*)hh->F[0];
+      d.F1 = (T*)hh->F[1];
+      d.F2 = (T*)hh->F[2];
+      d.nsteps = b->nsteps[order[q]];
+      rd.push_back(d);
+    }
+    c.smem = 0;
+    auto make_tasks = [&](int B) {
+      tasks.clear();
+      for (size_t q = i; q < j; ++q) {
+        const int Z = b->h[order[q]]->cfg.Z;
+        for (int s0 = 0; s0 < Z; s0 += B) tasks.push_back(SodTask{(int)(q - i), s0});
+      }
+    };
+    if (cudaMalloc(&c.runs_dev, sizeof(SodRunDesc<T>) * rd.size()) != cudaSuccess)
+      return set_error(RSLB_ERR_ALLOC, "rslb_sod_batch_init: cudaMalloc failed");
+    cudaMemcpy(c.runs_dev, rd.data(), sizeof(SodRunDesc<T>) * rd.size(), cudaMemcpyHostToDevice);
+    // candidate tile kernels for this V (the automatic choice first)
+    std::vector<int> cands = {c.B};
+    if (autotune) {
+      const int alt[] = {28, 32, 16, 8};
+      for (int B : alt)
+        if (B != c.B && sod_stage_smem_bytes(b->fp64, B, V, QL, nm) > 0 &&
+            sod_stage_smem_bytes(b->fp64, B, V, QL, nm) <= (size_t)max_smem &&
+            !(B == 28 && (V < 128 || nm > 8)))
+          cands.push_back(B);
+    }
+    float best = 1e30f;
+    int bestB = c.B, bestK = 1;
+    for (int B : cands) {
+      make_tasks(B);
+      SodTask* td = nullptr;
+      if (cudaMalloc((void**)&td, sizeof(SodTask) * tasks.size()) != cudaSuccess)
+        return set_error(RSLB_ERR_ALLOC, "rslb_sod_batch_init: cudaMalloc failed");
+      cudaMemcpy(td, tasks.data(), sizeof(SodTask) * tasks.size(), cudaMemcpyHostToDevice);
+      const size_t smem = sod_stage_smem_bytes(b->fp64, B, V, QL, nm);
+      const int maxk = (smem * 2 + 4096 <= (size_t)max_smem + 1024) ? 2 : 1;
+      for (int k = 1; k <= (autotune ? maxk : 1); ++k) {
+        float ms = 0.f;
+        if (autotune) {
+          cudaEvent_t e0, e1;
+          cudaEventCreate(&e0);
+          cudaEventCreate(&e1);
+          // stage 0 reads F0 and writes F1 only: safe to repeat
+          sod_batch_stage_launch<T>(B, smem, k * b->nsm, (const SodRunDesc<T>*)c.runs_dev, td,
+                                    (int)tasks.size(), b->step_dev, 0, b->err, V, b->stream);
+          cudaEventRecord(e0, b->stream);
+          for (int rep = 0; rep < 3; ++rep)
+            sod_batch_stage_launch<T>(B, smem, k * b->nsm, (const SodRunDesc<T>*)c.runs_dev, td,
+                                      (int)tasks.size(), b->step_dev, 0, b->err, V, b->stream);
+          cudaEventRecord(e1, b->stream);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&ms, e0, e1);
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+        }
+        if (!autotune || ms < best) {
+          best = ms;
+          bestB = B;
+          bestK = k;
+        }
+      }
+      cudaFree(td);
+    }
+    c.B = bestB;
+    c.ctas_per_sm = bestK;
+    c.smem = sod_stage_smem_bytes(b->fp64, bestB, V, QL, nm);
+    make_tasks(bestB);
+    c.ntasks = (int)tasks.size();
+    if (cudaMalloc((void**)&c.tasks_dev, sizeof(SodTask) * tasks.size()) != cudaSuccess)
+      return set_error(RSLB_ERR_ALLOC, "rslb_sod_batch_init: cudaMalloc failed");
+    cudaMemcpy(c.tasks_dev, tasks.data(), sizeof(SodTask) * tasks.size(), cudaMemcpyHostToDevice);
+    b->cls.push_back(c);
+    i = j;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_error(e, "rslb_sod_batch_init: tuning");
+  // tuning launches changed only F1; clear the error word they may have set
+  cudaMemset(b->err, 0, 2 * sizeof(int));
+  return RSLB_OK;
+}
+
+}  // namespace
+
+extern "C" int rslb_sod_batch_init(rslb_sod_batch** out, const rslb_sod_run* runs, int nruns,
+                                   const rslb_sod_batch_opts* o, void* stream) {
+  clear_error();
+  if (!out || !runs || !o || nruns < 1)
+    return set_error(RSLB_ERR_ARG, "rslb_sod_batch_init: NULL argument or nruns < 1");
+  *out = nullptr;
+  if (o->Q_L < 1 || o->Q_L > 8 || (o->precision != RSLB_F32 && o->precision != RSLB_F64) ||
+      (o->bc != RSLB_BC_FIXED_EQ && o->bc != RSLB_BC_OUTFLOW) || !(o->z_max > o->z_min) ||
+      !(o->cfl > 0.0 && o->cfl < 1.0) || !(o->dt_over_tau > 0.0 && o->dt_over_tau < 1.0))
+    return set_error(RSLB_ERR_ARG, "rslb_sod_batch_init: invalid options");
+  rslb_sod_batch* b = new rslb_sod_batch();
+  b->nruns = nruns;
+  b->fp64 = o->precision == RSLB_F64;
+  b->stream = (cudaStream_t)stream;
+  b->step_dev = nullptr;
+  b->err = nullptr;
+  b->steps_done = 0;
+  b->max_steps = 0;
+  b->total_cv = 0.0;
+  b->graph = nullptr;
+  b->graph_failed = false;
+  int rc = RSLB_OK;
+  for (int r = 0; r < nruns && !rc; ++r) {
+    const rslb_sod_run& R = runs[r];
+    if (R.Z < 1 || R.Q_xi < 2 || !(R.tau > 0.0) || !(R.t_end > 0.0)) {
+      rc = set_error(RSLB_ERR_ARG, "rslb_sod_batch_init: run %d: invalid parameters", r);
+      break;
+    }
+    std::vector<double> xi(R.Q_xi), w(R.Q_xi);
+    gauss_legendre_host(R.Q_xi, xi.data(), w.data());
+    const double dz = (o->z_max - o->z_min) / R.Z;
+    const double dtmax = std::fmin(o->cfl * dz / std::fabs(xi[R.Q_xi - 1]), o->dt_over_tau * R.tau);
+    const long long ns = (long long)std::ceil(R.t_end / dtmax - 1e-12);
+    rslb_config c{};
+    c.Z = R.Z;
+    c.z_min = o->z_min;
+    c.z_max = o->z_max;
+    c.Q_xi = R.Q_xi;
+    c.Q_L = o->Q_L;
+    c.N_Omega = o->N_Omega >= 0 ? o->N_Omega : std::min(R.Q_xi - 1, 5);
+    c.precision = o->precision;
+    c.bc = o->bc;
+    c.tau_mode = RSLB_TAU_CONST;
+    c.tau = R.tau;
+    c.lambda_ref = 1.0;
+    c.dt = R.t_end / (double)ns;
+    c.nL = R.nL;
+    c.TL = R.TL;
+    c.nR = R.nR;
+    c.TR = R.TR;
+    rslb_handle* hh = nullptr;
+    rc = rslb_init(&hh, &c, stream);
+    if (rc) {
+      set_error(rc, "rslb_sod_batch_init: run %d: %s", r, rslb::last_error());
+      break;
+    }
+    b->h.push_back(hh);
+    b->nsteps.push_back(ns);
+    b->max_steps = std::max(b->max_steps, ns);
+    b->total_cv += (double)ns * R.Z * (double)hh->V;
+  }
+  if (!rc && cudaMalloc((void**)&b->step_dev, sizeof(long long)) != cudaSuccess)
+    rc = set_error(RSLB_ERR_ALLOC, "rslb_sod_batch_init: cudaMalloc failed");
+  if (!rc && cudaMalloc((void**)&b->err, 2 * sizeof(int)) != cudaSuccess)
+    rc = set_error(RSLB_ERR_ALLOC, "rslb_sod_batch_init: cudaMalloc failed");
+  if (!rc) {
+    cudaMemset(b->step_dev, 0, sizeof(long long));
+    cudaMemset(b->err, 0, 2 * sizeof(int));
+    rc = b->fp64 ? batch_build_classes<double>(b, o->autotune)
+                 : batch_build_classes<float>(b, o->autotune);
+  }
+  if (rc) {
+    batch_free(b);
+    return rc;
+  }
+  *out = b;
+  return RSLB_OK;
+}
+
+extern "C" int rslb_sod_batch_step(rslb_sod_batch* b, int nsteps) {
+  clear_error();
+  if (!b || nsteps < 0) return set_error(RSLB_ERR_ARG, "rslb_sod_batch_step: bad arguments");
+  cudaError_t e = cudaSuccess;
+  int rest = nsteps;
+  if (b->stream != nullptr && nsteps >= kGraphSteps && !b->graph_failed) {
+    if (!b->graph) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      cudaError_t le = cudaSuccess;
+      if (e == cudaSuccess) {
+        le = b->fp64 ? batch_enqueue<double>(b, kGraphSteps) : batch_enqueue<float>(b, kGraphSteps);
+        e = cudaStreamEndCapture(b->stream, &g);
+      }
+      if (le != cudaSuccess) e = le;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->graph = nullptr;
+        b->graph_failed = true;
+        cudaGetLastError();
+        e = cudaSuccess;
+      }
+    }
+    while (b->graph && rest >= kGraphSteps && e == cudaSuccess) {
+      e = cudaGraphLaunch(b->graph, b->stream);
+      rest -= kGraphSteps;
+    }
+  }
+  if (e == cudaSuccess && rest > 0)
+    e = b->fp64 ? batch_enqueue<double>(b, rest) : batch_enqueue<float>(b, rest);
+  if (e != cudaSuccess) return cuda_error(e, "rslb_sod_batch_step");
+  b->steps_done += nsteps;
+  return RSLB_OK;
+}
+
+extern "C" int rslb_sod_batch_info(const rslb_sod_batch* b, long long* max_steps,
+                                   long long* steps_done, double* total_cv_updates) {
+  clear_error();
+  if (!b) return set_error(RSLB_ERR_ARG, "rslb_sod_batch_info: NULL batch");
+  if (max_steps) *max_steps = b->max_steps;
+  if (steps_done) *steps_done = b->steps_done;
+  if (total_cv_updates) *total_cv_updates = b->total_cv;
+  return RSLB_OK;
+}
+
+extern "C" int rslb_sod_batch_run_info(const rslb_sod_batch* b, int run, long long* nsteps,
+                                       double* dt) {
+  clear_error();
+  if (!b || run < 0 || run >= b->nruns)
+    return set_error(RSLB_ERR_ARG, "rslb_sod_batch_run_info: bad run");
+  if (nsteps) *nsteps = b->nsteps[run];
+  if (dt) *dt = b->h[run]->cfg.dt;
+  return RSLB_OK;
+}
+
+extern "C" int rslb_sod_batch_tuning(const rslb_sod_batch* b, int g, int* V, int* tile_cells,
+                                     int* ctas_per_sm) {
+  clear_error();
+  if (!b || g < 0 || g >= (int)b->cls.size())
+    return set_error(RSLB_ERR_ARG, "rslb_sod_batch_tuning: bad group");
+  if (V) *V = b->cls[g].V;
+  if (tile_cells) *tile_cells = b->cls[g].B;
+  if (ctas_per_sm) *ctas_per_sm = b->cls[g].ctas_per_sm;
+  return RSLB_OK;
+}
+
+extern "C" int rslb_sod_batch_moments(rslb_sod_batch* b, int run, double* out) {
+  clear_error();
+  if (!b || run < 0 || run >= b->nruns || !out)
+    return set_error(RSLB_ERR_ARG, "rslb_sod_batch_moments: bad arguments");
+  int herr[2] = {0, 0};
+  cudaMemcpyAsync(herr, b->err, sizeof(herr), cudaMemcpyDeviceToHost, b->stream);
+  cudaStreamSynchronize(b->stream);
+  if (herr[0])
+    return set_error(RSLB_ERR_NONPHYSICAL, "rslb_sod_batch: non-physical state (cell %d of a run)",
+                     herr[1]);
+  return rslb_moments(b->h[run], out, 0);
+}
+
+extern "C" void rslb_sod_batch_destroy(rslb_sod_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
 }

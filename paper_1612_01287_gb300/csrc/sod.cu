@@ -278,10 +278,10 @@ __device__ __forceinline__ void sweep_segment(const T* row, T* orow, int i0, T x
 }
 
 template <typename T, int B, int NT>
-__global__ void __launch_bounds__(NT, 2)
-sod_stage_kernel(const T* __restrict__ fin, const T* __restrict__ fn, T* fout, int stage,
-                 int* err, SodGeom g, SodTables<T> tb, const int* __restrict__ rowv, int nneg,
-                 int nseg) {
+__device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __restrict__ fn,
+                                         T* fout, int stage, int* err, const SodGeom& g,
+                                         const SodTables<T>& tb, const int* __restrict__ rowv,
+                                         int nneg, int nseg, int s0) {
   constexpr int VN = V16<T>::n;
   constexpr int W = B + 2 * kHalo;
   constexpr int P = tile_pitch<T>(W);
@@ -298,7 +298,6 @@ sod_stage_kernel(const T* __restrict__ fin, const T* __restrict__ fn, T* fout, i
   T* gco = reinterpret_cast<T*>(smem_raw + lay.gco);
   const int MP = coef_pitch<T>(g.nm);
 
-  const int s0 = blockIdx.x * B;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
 
@@ -512,6 +511,30 @@ sod_stage_kernel(const T* __restrict__ fin, const T* __restrict__ fn, T* fout, i
 }
 
 template <typename T, int B, int NT>
+__global__ void __launch_bounds__(NT, 2)
+sod_stage_kernel(const T* __restrict__ fin, const T* __restrict__ fn, T* fout, int stage,
+                 int* err, SodGeom g, SodTables<T> tb, const int* __restrict__ rowv, int nneg,
+                 int nseg) {
+  sod_tile<T, B, NT>(fin, fn, fout, stage, err, g, tb, rowv, nneg, nseg, blockIdx.x * B);
+}
+
+template <typename T, int B, int NT>
+__global__ void __launch_bounds__(NT, 2)
+sod_batch_kernel(const SodRunDesc<T>* __restrict__ runs, const SodTask* __restrict__ tasks,
+                 int ntasks, const long long* __restrict__ step, int stage, int* err, int nseg) {
+  const long long n = *step;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SodTask tk = tasks[t];
+    const SodRunDesc<T> R = runs[tk.run];
+    if (n >= R.nsteps) break;  // tasks are ordered by decreasing step count
+    const T* fin = stage == 0 ? R.F0 : (stage == 1 ? R.F1 : R.F2);
+    T* fout = stage == 0 ? R.F1 : (stage == 1 ? R.F2 : R.F0);
+    sod_tile<T, B, NT>(fin, R.F0, fout, stage, err, R.g, R.tb, R.rowv, R.nneg, nseg, tk.s0);
+    __syncthreads();
+  }
+}
+
+template <typename T, int B, int NT>
 static size_t smem_for(int V, int QL, int nm, int nseg) {
   return SodSmem<T>(V, B, QL, nm, nseg > 1).total;
 }
@@ -522,11 +545,32 @@ static int pick_nseg(int V, int B, int NT, int VN) {
   return nseg;
 }
 
+// Opt every stage kernel into the large dynamic shared-memory carve-out
+// (done once at set-up, outside any stream capture).
+cudaError_t sod_set_attributes() {
+  const void* fns[] = {(const void*)sod_stage_kernel<float, 32, 320>,
+                       (const void*)sod_stage_kernel<float, 16, 320>,
+                       (const void*)sod_stage_kernel<double, 16, 320>,
+                       (const void*)sod_stage_kernel<double, 8, 320>,
+                       (const void*)sod_batch_kernel<float, 32, 320>,
+                       (const void*)sod_batch_kernel<float, 16, 320>,
+                       (const void*)sod_batch_kernel<double, 16, 320>,
+                       (const void*)sod_batch_kernel<double, 8, 320>};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+  }
+  return sod32_set_attributes();
+}
+
 SodLaunch sod_pick_launch(bool fp64, int V, int QL, int nm, int max_smem) {
   SodLaunch L{0, 0};
   if (QL > kMaxQL || V < 1 || nm < 1 || nm > kMaxM) return L;
   const size_t half = (size_t)max_smem / 2 - 2048;
   if (!fp64) {
+    // packed FP32x2 kernel: whole rows per thread, so it needs enough rows to
+    // fill a CTA, N_Omega <= 7, and two CTAs per SM
+    if (V >= 128 && nm <= 8 && sod32_smem_bytes(V, QL) <= half) return {28, 0};
     const int n32 = pick_nseg(V, 32, 320, 4), n16 = pick_nseg(V, 16, 320, 4);
     if (smem_for<float, 32, 320>(V, QL, nm, n32) <= half) return {32, 0};
     if (smem_for<float, 16, 320>(V, QL, nm, n16) <= half) return {16, 0};
@@ -564,6 +608,9 @@ template <typename T>
 cudaError_t sod_stage_launch(const SodLaunch& L, const SodGeom& g, const SodTables<T>& tb,
                              const int* rowv, int nneg, const T* fin, const T* fn, T* fout,
                              int stage, int* err, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (L.B == 28) return sod32_stage_launch(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
+  }
   switch (L.B) {
     case 32:
       if constexpr (sizeof(T) == 4) return launch_b<T, 32>(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
@@ -585,6 +632,62 @@ template cudaError_t sod_stage_launch<double>(const SodLaunch&, const SodGeom&,
                                               const SodTables<double>&, const int*, int,
                                               const double*, const double*, double*, int, int*,
                                               cudaStream_t);
+
+size_t sod_stage_smem_bytes(bool fp64, int B, int V, int QL, int nm) {
+  if (!fp64) {
+    if (B == 28) return sod32_smem_bytes(V, QL);
+    if (B == 32) return smem_for<float, 32, 320>(V, QL, nm, pick_nseg(V, 32, 320, 4));
+    if (B == 16) return smem_for<float, 16, 320>(V, QL, nm, pick_nseg(V, 16, 320, 4));
+  } else {
+    if (B == 16) return smem_for<double, 16, 320>(V, QL, nm, pick_nseg(V, 16, 320, 2));
+    if (B == 8) return smem_for<double, 8, 320>(V, QL, nm, pick_nseg(V, 8, 320, 2));
+  }
+  return 0;
+}
+
+cudaError_t sod32_batch_launch(size_t smem, int grid, const SodRunDesc<float>* runs,
+                               const SodTask* tasks, int ntasks, const long long* step, int stage,
+                               int* err, cudaStream_t st);
+
+// Batched stages: all runs of a class share V (so nseg and the tile width).
+template <typename T>
+cudaError_t sod_batch_stage_launch(int B, size_t smem, int grid, const SodRunDesc<T>* runs,
+                                   const SodTask* tasks, int ntasks, const long long* step,
+                                   int stage, int* err, int V, cudaStream_t st) {
+  if (ntasks == 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    if (B == 28) return sod32_batch_launch(smem, grid, runs, tasks, ntasks, step, stage, err, st);
+    if (B == 32) {
+      sod_batch_kernel<T, 32, 320><<<grid, 320, smem, st>>>(runs, tasks, ntasks, step, stage, err,
+                                                           pick_nseg(V, 32, 320, 4));
+      return cudaGetLastError();
+    }
+    if (B == 16) {
+      sod_batch_kernel<T, 16, 320><<<grid, 320, smem, st>>>(runs, tasks, ntasks, step, stage, err,
+                                                           pick_nseg(V, 16, 320, 4));
+      return cudaGetLastError();
+    }
+  } else {
+    if (B == 16) {
+      sod_batch_kernel<T, 16, 320><<<grid, 320, smem, st>>>(runs, tasks, ntasks, step, stage, err,
+                                                           pick_nseg(V, 16, 320, 2));
+      return cudaGetLastError();
+    }
+    if (B == 8) {
+      sod_batch_kernel<T, 8, 320><<<grid, 320, smem, st>>>(runs, tasks, ntasks, step, stage, err,
+                                                          pick_nseg(V, 8, 320, 2));
+      return cudaGetLastError();
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t sod_batch_stage_launch<float>(int, size_t, int, const SodRunDesc<float>*,
+                                                   const SodTask*, int, const long long*, int,
+                                                   int*, int, cudaStream_t);
+template cudaError_t sod_batch_stage_launch<double>(int, size_t, int, const SodRunDesc<double>*,
+                                                    const SodTask*, int, const long long*, int,
+                                                    int*, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Initialisation: per-cell FP64 coefficients, then populations.

@@ -33,6 +33,28 @@ struct SodTables {
   const double* gl_w;  // [kAeqNodes]
 };
 
+// One run of a batch (batched stage kernels): geometry, tables and the three
+// population buffers; nsteps is the run's total step count.
+template <typename T>
+struct SodRunDesc {
+  SodGeom g;
+  SodTables<T> tb;
+  const int* rowv;
+  int nneg;
+  T* F0;
+  T* F1;
+  T* F2;
+  long long nsteps;
+};
+
+// One CTA task of a batched stage: a tile starting at cell s0 of run `run`.
+// Task lists are ordered by decreasing run step count, so the tasks still to
+// do at step n form a prefix.
+struct SodTask {
+  int run;
+  int s0;
+};
+
 // FP64 tables used by the initialisation and moment kernels.
 struct SodTablesF64 {
   const double* xi;   // [V]
@@ -50,6 +72,11 @@ struct SodLaunch {
   size_t smem;  // dynamic shared memory bytes
 };
 
+// Opt the stage kernels into large dynamic shared memory (call at set-up,
+// outside stream capture).
+cudaError_t sod_set_attributes();
+cudaError_t sod32_set_attributes();
+
 // Pick the tile width for V velocities; returns B = 0 if V does not fit.
 SodLaunch sod_pick_launch(bool fp64, int V, int QL, int nm, int max_smem);
 
@@ -60,6 +87,21 @@ template <typename T>
 cudaError_t sod_stage_launch(const SodLaunch& L, const SodGeom& g, const SodTables<T>& tb,
                              const int* rowv, int nneg, const T* fin, const T* fn, T* fout,
                              int stage, int* err, cudaStream_t st);
+
+// FP32 stage kernel with packed FP32x2 arithmetic (sod32.cu): 28-cell tiles,
+// N_Omega <= 7.  Shared-memory bytes for V velocities and Q_L radial nodes.
+size_t sod32_smem_bytes(int V, int QL);
+cudaError_t sod32_stage_launch(const SodGeom& g, const SodTables<float>& tb, const int* rowv,
+                               int nneg, const float* fin, const float* fn, float* fout, int stage,
+                               int* err, cudaStream_t st);
+
+// Batched stage launches: a persistent grid of `grid` CTAs walks the task list
+// (tile width B as chosen by sod_pick_launch / the tuner for this class).
+template <typename T>
+cudaError_t sod_batch_stage_launch(int B, size_t smem, int grid, const SodRunDesc<T>* runs,
+                                   const SodTask* tasks, int ntasks, const long long* step,
+                                   int stage, int* err, int V, cudaStream_t st);
+size_t sod_stage_smem_bytes(bool fp64, int B, int V, int QL, int nm);
 
 // Per-cell coefficients c''_{k,m} (FP64) of f^eq for given (n, T, beta) per
 // cell, then populations f[v*ldz + s] = sum_m c''_{k(v),m}(s) wp_m(v).

@@ -62,3 +62,20 @@ def random_smooth_fields(Z, seed=SEED, beta_max=0.6):
     T = 1.0 + a[1] * np.sin(2 * np.pi * z + ph[1])
     beta = beta_max * np.sin(2 * np.pi * z + ph[2])
     return n, T, beta
+
+
+def sod_sweep(nruns=4096, seed=SEED, z_lo=256, z_hi=8192, qxi=(8, 20, 50, 100, 200),
+              tau_lo=1e-4, tau_hi=10.0, t_end=0.8):
+    """Uneven batch of shock tubes: Z log-uniform in [z_lo, z_hi] (integer), Q_xi
+    drawn from ``qxi``, tau log-uniform, left chamber (n, P) = (1, 1), right
+    chamber density 1/8 and pressure 1/r with r uniform in [2, 20].  Returned as
+    a list of run dicts (keys of ``rslb_sod_run``)."""
+    rng = np.random.default_rng(seed + 4)
+    Z = np.exp(rng.uniform(math.log(z_lo), math.log(z_hi + 1), size=nruns)).astype(np.int64)
+    Z = np.clip(Z, z_lo, z_hi)
+    Q = rng.choice(np.asarray(qxi), size=nruns)
+    tau = np.exp(rng.uniform(math.log(tau_lo), math.log(tau_hi), size=nruns))
+    ratio = rng.uniform(2.0, 20.0, size=nruns)
+    nR = 0.125
+    return [dict(Z=int(Z[r]), Q_xi=int(Q[r]), tau=float(tau[r]), nL=1.0, TL=1.0, nR=nR,
+                 TR=float(1.0 / ratio[r] / nR), t_end=float(t_end)) for r in range(nruns)]

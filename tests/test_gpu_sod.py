@@ -115,6 +115,22 @@ def test_large_velocity_sets(precision, tol, Q_xi):
     sodcase.compare(case, 6, precision, tol, tol if precision == "f64" else None)
 
 
+@pytest.mark.parametrize("precision,tiles,tol", [("f32", (28, 32, 16), 1e-6),
+                                                 ("f64", (16, 8), 1e-13)])
+def test_tile_width_does_not_change_results(precision, tiles, tol):
+    from paper_1612_01287_gb300 import Sod
+    case = sodcase.gpu_kwargs(small_case())
+    case.update(Z=200, Q_xi=100)
+    out = []
+    for B in tiles:
+        with Sod(precision=precision, tile_cells=B, **case) as s:
+            s.step(20)
+            out.append(s.moments())
+    for other in out[1:]:
+        errs = sodcase.field_errors(other, out[0])
+        assert max(errs.values()) <= tol, errs
+
+
 def test_moving_states_negative_beta_fp64():
     """Boosted initial states (sgn(beta) enters f^eq through P_m(sgn(beta) xi))."""
     case = dict(Z=64, Q_xi=16, Q_L=3, N_Omega=6, bc="fixed_eq", tau=5e-3, dt=1e-3,
@@ -160,20 +176,6 @@ def test_full_size_sampled_cells(precision, tol):
     errs = sodcase.field_errors(got, ref)
     for k in sodcase.PARITY_FIELDS:
         assert errs[k] <= tol, (k, errs, samples)
-
-
-@pytest.mark.parametrize("precision,tiles,tol", [("f32", (32, 16), 1e-6), ("f64", (16, 8), 1e-13)])
-def test_tile_width_does_not_change_results(precision, tiles, tol):
-    from paper_1612_01287_gb300 import Sod
-    case = sodcase.gpu_kwargs(small_case())
-    case.update(Z=200, Q_xi=100)
-    out = []
-    for B in tiles:
-        with Sod(precision=precision, tile_cells=B, **case) as s:
-            s.step(20)
-            out.append(s.moments())
-    errs = sodcase.field_errors(out[1], out[0])
-    assert max(errs.values()) <= tol, errs
 
 
 def test_checkpoint_resume_is_bitwise():
@@ -222,3 +224,25 @@ def test_nonphysical_state_reported():
         with pytest.raises(RslbError) as ei:
             s.sync()
         assert ei.value.code == 6 and "cell" in str(ei.value)
+
+
+def test_graph_captured_steps_match_plain_launches():
+    """On a non-default stream rslb_step replays a captured graph of 8 steps;
+    the result is bitwise the one of plain launches."""
+    import torch
+    from paper_1612_01287_gb300 import Sod
+    case = sodcase.gpu_kwargs(small_case())
+    with Sod(precision="f32", **case) as a:
+        a.step(20)
+        ref = a.get_state()
+    s = torch.cuda.Stream()
+    with Sod(precision="f32", stream=s, **case) as b:
+        b.step(20)
+        b.step(3)
+        b.step(16)
+        got = b.get_state()
+    with Sod(precision="f32", **case) as c:
+        c.step(39)
+        ref39 = c.get_state()
+    np.testing.assert_array_equal(got, ref39)
+    assert not np.array_equal(ref, ref39)
