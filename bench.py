@@ -188,7 +188,7 @@ def bench_bjorken(stream, steps=None):
     cv = 3 * int(qxi.sum())
     flops = 3 * 2 * 3 * float((qxi.astype(np.float64) ** 2).sum())  # K^P contraction only
     out = {"runs": len(qxi), "cv_per_step": cv, "kp_flops_per_step": flops}
-    for mode in ("simt",):
+    for mode in ("simt", "tf32x3"):
         with Bjorken(qxi, "parton", taus, Q_L=3, precision="f32", kp_mode=mode, dtau=1e-3,
                      stream=stream) as b:
             b.step(1)
