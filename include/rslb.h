@@ -375,6 +375,79 @@ int rslb_bjorken_kp_apply(rslb_bjorken* b, void* y);
 /* Release everything owned by b (synchronises).  NULL is a no-op. */
 void rslb_bjorken_destroy(rslb_bjorken* b);
 
+/* ------------------------------------------------------------------------ */
+/* Learned closure of a low-order velocity set (an addition to the paper's  */
+/* method).  A per-cell MLP, trained on data generated by the method with a */
+/* high-order velocity set, corrects the low-order populations after every  */
+/* RK3 step; the correction leaves each cell's N^t, T^tt, T^tz unchanged.   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct rslb_mlp rslb_mlp;
+
+/*
+ * Network n_in -> n_hidden -> n_hidden -> n_out, SiLU after both hidden
+ * layers, BF16 weights (an FP32 master copy is kept for training), FP32
+ * biases and accumulation.  Parameters (flat FP32 vector, this order):
+ * W1 [n_hidden][n_in], b1 [n_hidden], W2 [n_hidden][n_hidden], b2 [n_hidden],
+ * W3 [n_out][n_hidden], b3 [n_out]; initialised from `seed` (weights normal
+ * with variance 1/fan_in, the output layer scaled by 0.1, biases zero).
+ * Limits: n_in <= 128, n_hidden in {16, 32, 64}, n_out <= 32.
+ * Errors: RSLB_ERR_ARG, RSLB_ERR_UNSUPPORTED, RSLB_ERR_ALLOC, RSLB_ERR_CUDA.
+ */
+int rslb_mlp_create(rslb_mlp** m, int n_in, int n_hidden, int n_out, unsigned long long seed,
+                    void* stream);
+int rslb_mlp_num_params(const rslb_mlp* m);
+/* Master parameters to / from caller-owned host memory (set resets Adam). */
+int rslb_mlp_get_params(rslb_mlp* m, float* theta);
+int rslb_mlp_set_params(rslb_mlp* m, const float* theta);
+
+/* Y [n][n_out] = net(X [n][n_in]); device pointers; asynchronous. */
+int rslb_mlp_forward(rslb_mlp* m, const float* X, int n, float* Y);
+
+/*
+ * Mean-squared loss L = sum (y - t)^2 / (n n_out) over the n samples
+ * (X [n][n_in], T [n][n_out], device) and its gradient with respect to the
+ * parameters, by the library's backward kernels (weights as used in the
+ * forward pass, i.e. BF16-rounded).  loss: host; grad: host, or NULL.
+ * Synchronises.
+ */
+int rslb_mlp_loss_grad(rslb_mlp* m, const float* X, const float* T, int n, double* loss,
+                       float* grad);
+
+/*
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8) on minibatches of `batch` samples,
+ * reshuffled each epoch from `seed`; epoch_loss (host, `epochs` entries, or
+ * NULL) receives each epoch's mean loss.  Synchronises.
+ */
+int rslb_mlp_train(rslb_mlp* m, const float* X, const float* T, int n, int epochs, int batch,
+                   double lr, unsigned long long seed, double* epoch_loss);
+void rslb_mlp_destroy(rslb_mlp* m);
+
+/*
+ * State of `lo` := R(state of `hi`): per radial node, the Legendre moments
+ * m < Q_xi(lo) of the high-order populations re-expanded at the low-order
+ * nodes, f^lo_{ik} = w_i sum_m (2m+1)/2 P_m(xi_i) sum_j P_m(xi_j) f^hi_{jk}
+ * (Gauss-Legendre exactness keeps the moments of Eq. macro_jk).  Both
+ * handles RSLB_F32 with equal Z and Q_L.  Synchronises.
+ */
+int rslb_restrict(rslb_handle* hi, rslb_handle* lo);
+
+/*
+ * One training sample per cell: lo := R(hi); X [Z][3V+1] (device) = features
+ * of lo (populations of cells s-1, s, s+1 over n_s, then log10 tau, outflow
+ * copies at the ends); then both handles advance one RK3 step and
+ * T [Z][V] (device) = P(R(hi) - lo) / n_s with P the projection that removes
+ * the components along the collision invariants (1, p, p xi) weighted by
+ * w_j w_k.  V = Q_L Q_xi(lo) <= 32.  Synchronises.
+ */
+int rslb_closure_sample(rslb_handle* hi, rslb_handle* lo, double tau, float* X, float* T);
+
+/*
+ * nsteps RK3 steps of `lo`, each followed by f += P(n_s net(features)) in
+ * every cell.  The network must be (3V+1) -> V.  Asynchronous.
+ */
+int rslb_closure_step(rslb_handle* lo, rslb_mlp* m, double tau, int nsteps);
+
 /* Description of the last failure in the calling thread ("" if none). */
 const char* rslb_last_error(void);
 

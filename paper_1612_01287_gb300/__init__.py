@@ -5,4 +5,5 @@ The compute path is the CUDA library ``_build/librslb.so`` behind the C ABI of
 binding with the same names.
 """
 from . import build
-from ._lib import FIELDS, Bjorken, RslbError, Sod, SodBatch, load, quadrature  # noqa: F401
+from ._lib import (FIELDS, MLP, Bjorken, RslbError, Sod, SodBatch, closure_sample,  # noqa: F401
+                   closure_step, load, quadrature, restrict)

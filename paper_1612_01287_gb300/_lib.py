@@ -462,3 +462,105 @@ class SodBatch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _mlp_sigs(L):
+    if getattr(L, "_mlp_ready", False):
+        return
+    i, p, d, u64 = ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_ulonglong
+    for name, (res, args) in {
+        "rslb_mlp_create": (i, [ctypes.POINTER(p), i, i, i, u64, p]),
+        "rslb_mlp_num_params": (i, [p]),
+        "rslb_mlp_get_params": (i, [p, p]),
+        "rslb_mlp_set_params": (i, [p, p]),
+        "rslb_mlp_forward": (i, [p, p, i, p]),
+        "rslb_mlp_loss_grad": (i, [p, p, p, i, ctypes.POINTER(d), p]),
+        "rslb_mlp_train": (i, [p, p, p, i, i, i, d, u64, p]),
+        "rslb_mlp_destroy": (None, [p]),
+        "rslb_restrict": (i, [p, p]),
+        "rslb_closure_sample": (i, [p, p, d, p, p]),
+        "rslb_closure_step": (i, [p, p, d, i]),
+    }.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    L._mlp_ready = True
+
+
+class MLP:
+    """The closure network (``rslb_mlp``); arrays passed as device pointers
+    (ints, e.g. ``tensor.data_ptr()``) unless noted."""
+
+    def __init__(self, n_in, n_hidden, n_out, seed=0, stream=None):
+        L = load()
+        _mlp_sigs(L)
+        self.n_in, self.n_hidden, self.n_out = int(n_in), int(n_hidden), int(n_out)
+        self._h = ctypes.c_void_p()
+        _check(L.rslb_mlp_create(ctypes.byref(self._h), self.n_in, self.n_hidden, self.n_out,
+                                 int(seed), _stream_ptr(stream)))
+        self.num_params = L.rslb_mlp_num_params(self._h)
+
+    def get_params(self):
+        t = np.zeros(self.num_params, dtype=np.float32)
+        _check(load().rslb_mlp_get_params(self._h, _ptr(t)))
+        return t
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == self.num_params
+        _check(load().rslb_mlp_set_params(self._h, _ptr(t)))
+
+    def forward(self, X_ptr, n, Y_ptr):
+        _check(load().rslb_mlp_forward(self._h, ctypes.c_void_p(X_ptr), int(n),
+                                       ctypes.c_void_p(Y_ptr)))
+
+    def loss_grad(self, X_ptr, T_ptr, n):
+        loss = ctypes.c_double()
+        g = np.zeros(self.num_params, dtype=np.float32)
+        _check(load().rslb_mlp_loss_grad(self._h, ctypes.c_void_p(X_ptr), ctypes.c_void_p(T_ptr),
+                                         int(n), ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train(self, X_ptr, T_ptr, n, epochs, batch=4096, lr=1e-3, seed=0):
+        losses = np.zeros(max(int(epochs), 1))
+        _check(load().rslb_mlp_train(self._h, ctypes.c_void_p(X_ptr), ctypes.c_void_p(T_ptr),
+                                     int(n), int(epochs), int(batch), float(lr), int(seed),
+                                     _ptr(losses)))
+        return losses[:int(epochs)]
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().rslb_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def restrict(hi, lo):
+    """State of Sod handle ``lo`` := restriction of ``hi``'s state."""
+    L = load()
+    _mlp_sigs(L)
+    _check(L.rslb_restrict(hi._h, lo._h))
+
+
+def closure_sample(hi, lo, tau, X_ptr, T_ptr):
+    L = load()
+    _mlp_sigs(L)
+    _check(L.rslb_closure_sample(hi._h, lo._h, float(tau), ctypes.c_void_p(X_ptr),
+                                 ctypes.c_void_p(T_ptr)))
+
+
+def closure_step(lo, mlp, tau, nsteps=1):
+    L = load()
+    _mlp_sigs(L)
+    _check(L.rslb_closure_step(lo._h, mlp._h, float(tau), int(nsteps)))

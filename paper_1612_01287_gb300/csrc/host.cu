@@ -646,6 +646,23 @@ extern "C" int rslb_set_state(rslb_handle* h, const void* f, int on_device) {
   return RSLB_OK;
 }
 
+namespace rslb {
+int sod_view(rslb_handle* h, SodView* v) {
+  if (!h || !v) return RSLB_ERR_ARG;
+  v->Z = h->cfg.Z;
+  v->ldz = h->ldz;
+  v->V = h->V;
+  v->Q_xi = h->cfg.Q_xi;
+  v->Q_L = h->cfg.Q_L;
+  v->fp64 = h->fp64;
+  v->stream = h->stream;
+  v->F0 = h->F[0];
+  v->F1 = h->F[1];
+  v->dt = h->cfg.dt;
+  return RSLB_OK;
+}
+}  // namespace rslb
+
 extern "C" int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* threads) {
   clear_error();
   if (!h) return set_error(RSLB_ERR_ARG, "rslb_launch_info: NULL handle");

@@ -1,0 +1,204 @@
+"""Learned closure on the GPU against the FP64 reference (oracle/closure.py):
+restriction, MLP forward, backward (gradient) and the conserving correction;
+then a small end-to-end training run that must lower the low-order error."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closure as C
+from paper_1612_01287_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+QL, QLO, QHI = 3, 8, 200
+V = QL * QLO
+D, H, O = 3 * V + 1, 64, V
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_01287_gb300 import build, load
+    build.build()
+    load()
+
+
+def sod_pair(Z, tau, dt, fields=None, bc="outflow"):
+    from paper_1612_01287_gb300 import Sod
+    kw = dict(Z=Z, Q_L=QL, N_Omega=5, precision="f32", bc=bc, tau=tau, dt=dt)
+    if fields is not None:
+        kw["fields"] = fields
+    return Sod(Q_xi=QHI, **kw), Sod(Q_xi=QLO, **kw)
+
+
+def oracle_theta(theta):
+    """The parameters as the GPU uses them: BF16 weights, FP32 biases."""
+    s = C.param_sizes(D, H, O)
+    out, o = [], 0
+    for k, n in enumerate(s):
+        part = np.asarray(theta[o:o + n], dtype=np.float32)
+        out.append(C.bf16_round(part) if k % 2 == 0 else part.astype(np.float64))
+        o += n
+    return np.concatenate(out)
+
+
+def test_restriction_matches_oracle():
+    from paper_1612_01287_gb300 import restrict
+    Z = 96
+    n, T, b = workloads.random_smooth_fields(Z, beta_max=0.5)
+    hi, lo = sod_pair(Z, 0.05, 1e-3, fields=(n, T, b))
+    with hi, lo:
+        hi.step(5)
+        fh = hi.get_state().astype(np.float64).T  # [Z][V_hi]
+        restrict(hi, lo)
+        fl = lo.get_state().astype(np.float64).T
+    ref = C.restrict(fh, QHI, QLO, QL)
+    assert np.abs(fl - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+def test_mlp_forward_matches_oracle():
+    import torch
+    from paper_1612_01287_gb300 import MLP
+    rng = np.random.default_rng(1)
+    X = rng.normal(0, 1, size=(300, D)).astype(np.float32)
+    with MLP(D, H, O, seed=7) as m:
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.zeros((300, O), dtype=torch.float32, device="cuda")
+        m.forward(Xd.data_ptr(), 300, Yd.data_ptr())
+        torch.cuda.synchronize()
+        th = oracle_theta(m.get_params())
+    ref, _ = C.forward(th, X.astype(np.float64), D, H, O)
+    got = Yd.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_mlp_gradient_matches_oracle():
+    """Backward kernels vs FP64 backprop (all parameters) and vs the oracle's
+    central differences on 1000 random parameters: relative error <= 1e-3."""
+    import torch
+    from paper_1612_01287_gb300 import MLP
+    rng = np.random.default_rng(2)
+    N = 256
+    X = rng.normal(0, 1, size=(N, D)).astype(np.float32)
+    T = rng.normal(0, 0.1, size=(N, O)).astype(np.float32)
+    with MLP(D, H, O, seed=3) as m:
+        theta = m.get_params()
+        theta[-O:] = rng.normal(0, 0.1, size=O)  # non-zero output biases
+        theta[D * H:D * H + H] = rng.normal(0, 0.1, size=H)
+        m.set_params(theta)
+        Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+        loss, g = m.loss_grad(Xd.data_ptr(), Td.data_ptr(), N)
+        th = oracle_theta(m.get_params())
+    Lr, gr = C.loss_grad(th, X.astype(np.float64), T.astype(np.float64), D, H, O)
+    assert abs(loss - Lr) <= 1e-5 * Lr
+    rel = np.abs(g - gr).max() / np.abs(gr).max()
+    print("gradient vs FP64 backprop:", rel)
+    assert rel <= 1e-3
+    idx = rng.choice(len(th), size=1000, replace=False)
+    fd = C.fd_grad(th, X.astype(np.float64), T.astype(np.float64), D, H, O, idx, h=1e-4)
+    rel_fd = np.abs(g[idx] - fd).max() / np.abs(fd).max()
+    print("gradient vs oracle finite differences:", rel_fd)
+    assert rel_fd <= 1e-3
+
+
+def test_closure_sample_matches_oracle():
+    import torch
+    from paper_1612_01287_gb300 import closure_sample
+    Z, tau, dt = 64, 0.02, 2e-3
+    n, T0, b = workloads.random_smooth_fields(Z, beta_max=0.4)
+    hi, lo = sod_pair(Z, tau, dt, fields=(n, T0, b))
+    with hi, lo:
+        hi.step(3)
+        f0 = hi.get_state().astype(np.float64).T
+        Xd = torch.zeros((Z, D), device="cuda")
+        Td = torch.zeros((Z, O), device="cuda")
+        closure_sample(hi, lo, tau, Xd.data_ptr(), Td.data_ptr())
+        X, T = Xd.cpu().numpy(), Td.cpu().numpy()
+    r0 = C.restrict(f0, QHI, QLO, QL)
+    assert np.abs(X - C.features(r0, tau)).max() <= 2e-6 * np.abs(X[:, :-1]).max()
+    ph = oracle.sod_params(Z, QHI, QL, 5, bc="outflow", tau=tau, dt=dt)
+    pl = oracle.sod_params(Z, QLO, QL, 5, bc="outflow", tau=tau, dt=dt)
+    f1 = oracle.sod_steps(ph, f0, 1)
+    pred = oracle.sod_steps(pl, r0, 1)
+    Tref = C.project(C.restrict(f1, QHI, QLO, QL) - pred, QLO, QL) / r0.sum(1)[:, None]
+    scale = np.abs(r0).max() / r0.sum(1).min()
+    assert np.abs(T - Tref).max() <= 2e-6 * scale
+
+
+def test_closure_step_matches_oracle_and_conserves():
+    from paper_1612_01287_gb300 import MLP, Sod, closure_step
+    Z, tau, dt = 80, 0.05, 2e-3
+    n, T0, b = workloads.random_smooth_fields(Z, beta_max=0.4)
+    kw = dict(Z=Z, Q_xi=QLO, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", tau=tau, dt=dt,
+              fields=(n, T0, b))
+    with MLP(D, H, O, seed=5) as m, Sod(**kw) as a, Sod(**kw) as c:
+        th = m.get_params()
+        th[D * H + H + H * H + H:] *= 10.0  # a visible correction
+        m.set_params(th)
+        a.step(1)
+        closure_step(c, m, tau, 1)
+        fa = a.get_state().astype(np.float64).T
+        fc = c.get_state().astype(np.float64).T
+        thr = oracle_theta(m.get_params())
+    d = fc - fa
+    ref = C.correction(thr, fa, tau, QLO, QL, H)
+    assert np.abs(ref).max() > 1e-4 * np.abs(fa).max()
+    assert np.abs(d - ref).max() <= 1e-5 * np.abs(fa).max()
+    Phi, _ = C.invariants(QLO, QL)
+    inv_a, inv_c = fa @ Phi, fc @ Phi
+    assert np.abs(inv_c - inv_a).max() <= 2e-6 * np.abs(inv_a).max()
+
+
+def test_trained_closure_lowers_low_order_error():
+    """Train on data the high-order method generates (Q_xi = 200, tau in
+    {0.01, 0.1, 1}), then run Q_xi = 8 with and without the closure from the
+    shock-tube state and compare L2 errors of e and beta against Q_xi = 200."""
+    import torch
+    from paper_1612_01287_gb300 import MLP, Sod, closure_sample, closure_step
+    Z, t_end = 512, 0.2
+    dz = 2.0 / Z
+    dt = 0.5 * dz / 0.9999
+    nsteps = int(round(t_end / dt))
+    taus = (0.01, 0.1, 1.0)
+    Xs, Ts = [], []
+    for tau in taus:
+        hi, lo = sod_pair(Z, tau, dt)
+        with hi, lo:
+            for _ in range(nsteps):
+                Xd = torch.zeros((Z, D), device="cuda")
+                Td = torch.zeros((Z, O), device="cuda")
+                closure_sample(hi, lo, tau, Xd.data_ptr(), Td.data_ptr())
+                Xs.append(Xd)
+                Ts.append(Td)
+    X = torch.cat(Xs).contiguous()
+    T = torch.cat(Ts).contiguous()
+    N = X.shape[0]
+
+    def l2(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    res = {}
+    with MLP(D, H, O, seed=11) as m:
+        losses = m.train(X.data_ptr(), T.data_ptr(), N, epochs=30, batch=2048, lr=2e-3, seed=1)
+        print("training samples", N, "loss first/last epoch", losses[0], losses[-1])
+        assert losses[-1] < 0.5 * losses[0]
+        for tau in taus:
+            with Sod(Z=Z, Q_xi=QHI, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", tau=tau,
+                     dt=dt) as hi, \
+                    Sod(Z=Z, Q_xi=QLO, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", tau=tau,
+                        dt=dt) as lo, \
+                    Sod(Z=Z, Q_xi=QLO, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", tau=tau,
+                        dt=dt) as cl:
+                hi.step(nsteps)
+                lo.step(nsteps)
+                closure_step(cl, m, tau, nsteps)
+                mh, ml, mc = hi.moments(), lo.moments(), cl.moments()
+            res[tau] = {"plain": (l2(ml["E"], mh["E"]), l2(ml["beta"], mh["beta"])),
+                        "closure": (l2(mc["E"], mh["E"]), l2(mc["beta"], mh["beta"]))}
+    print("L2 errors (e, beta) vs Q_xi = 200:", res)
+    gain = [res[t]["closure"][0] < res[t]["plain"][0] for t in taus]
+    assert sum(gain) >= 2, res
