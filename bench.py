@@ -226,6 +226,75 @@ def bench_sod_batch(stream, steps=None):
             "cv_updates_to_t_end": total}
 
 
+def bench_closure(stream):
+    """Learned closure (Q_xi = 8 + MLP) against the plain high-order method
+    (Q_xi = 200).  Accuracy: shock tube on 2048 cells to t = 0.2, trained on
+    ~1e6 cell samples of Q_xi = 200 runs with tau in {0.03, 0.1, 0.3, 1, 3},
+    judged at tau in {0.1, 0.5 (not trained on), 1}.  Speed: per-step time of
+    each path on the 65536-cell tube."""
+    import torch
+    from paper_1612_01287_gb300 import MLP, Sod, closure_sample, closure_step
+    QL, QHI, QLO = 3, 200, 8
+    V = QL * QLO
+    D = 3 * V + 1
+    Z, t_end = 2048, 0.2
+    dt = 0.5 * (2.0 / Z) / 0.9999306
+    nsteps = int(round(t_end / dt))
+    kw = dict(Z=Z, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", dt=dt, stream=stream)
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    for tau in (0.03, 0.1, 0.3, 1.0, 3.0):
+        with Sod(Q_xi=QHI, tau=tau, **kw) as hi, Sod(Q_xi=QLO, tau=tau, **kw) as lo:
+            for n in range(0, nsteps, 4):
+                hi.step(3)
+                X = torch.empty((Z, D), device="cuda")
+                T = torch.empty((Z, V), device="cuda")
+                closure_sample(hi, lo, tau, X.data_ptr(), T.data_ptr())
+                Xs.append(X)
+                Ts.append(T)
+    X = torch.cat(Xs).contiguous()
+    T = torch.cat(Ts).contiguous()
+    del Xs, Ts
+    gen_s = time.perf_counter() - t0
+
+    def l2(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    out = {"samples": int(X.shape[0]), "datagen_s": gen_s, "cells": Z, "t_end": t_end,
+           "steps": nsteps, "network": "73-64-64-24 SiLU, BF16 weights, FP32 accumulate"}
+    with MLP(D, 64, V, seed=20161201, stream=stream) as m:
+        t0 = time.perf_counter()
+        losses = m.train(X.data_ptr(), T.data_ptr(), X.shape[0], epochs=12, batch=8192, lr=2e-3,
+                         seed=2)
+        out["train_s"] = time.perf_counter() - t0
+        out["loss_first_last"] = [float(losses[0]), float(losses[-1])]
+        acc = {}
+        for tau in (0.1, 0.5, 1.0):
+            with Sod(Q_xi=QHI, tau=tau, **kw) as hi, Sod(Q_xi=QLO, tau=tau, **kw) as lo, \
+                    Sod(Q_xi=QLO, tau=tau, **kw) as cl:
+                hi.step(nsteps)
+                lo.step(nsteps)
+                closure_step(cl, m, tau, nsteps)
+                mh, ml, mc = hi.moments(), lo.moments(), cl.moments()
+            acc[str(tau)] = {"plain_q8": {"e": l2(ml["E"], mh["E"]), "beta": l2(ml["beta"], mh["beta"])},
+                             "closure_q8": {"e": l2(mc["E"], mh["E"]),
+                                            "beta": l2(mc["beta"], mh["beta"])}}
+        out["l2_vs_q200"] = acc
+        # per-step time at 65536 cells
+        w = workloads.sod_large()
+        dtl = workload_dt(w)
+        big = dict(Z=w["Z"], Q_L=QL, N_Omega=5, precision="f32", bc="outflow", dt=dtl,
+                   tau=1.0, left=w["left"], right=w["right"], stream=stream)
+        with Sod(Q_xi=QHI, **big) as hi, Sod(Q_xi=QLO, **big) as cl:
+            hi.step(2)
+            closure_step(cl, m, 1.0, 2)
+            ms_hi = _timed(stream, hi.step, 8) / 8
+            ms_cl = _timed(stream, lambda k: closure_step(cl, m, 1.0, k), 8) / 8
+        out["ms_per_step_65536"] = {"q200_plain": ms_hi, "q8_closure": ms_cl,
+                                    "speedup": ms_hi / ms_cl}
+    return out
+
+
 def cpu_baseline(w, dt, steps=20, cells=2048):
     """The FP64 oracle on the host cores, on a bounded sample of the workload:
     `cells` cells around the membrane of one tube, all 600 velocities."""
@@ -399,7 +468,8 @@ def run_ours(args, rank, world, local_rank):
         t.close()
     extras = {}
     if rank == 0 and not args.no_side:
-        for name, fn in (("bjorken", bench_bjorken), ("sod_batch", bench_sod_batch)):
+        for name, fn in (("bjorken", bench_bjorken), ("sod_batch", bench_sod_batch),
+                         ("closure", bench_closure)):
             try:
                 extras[name] = fn(stream)
             except Exception as exc:  # a side measurement never sinks the headline line

@@ -27,7 +27,6 @@ namespace rslb {
 constexpr int kBjThreads = 256;
 constexpr int kBjMaxQ = 512;
 constexpr int kBjMaxQL = 8;
-constexpr int kTcMaxCols = 80;  // MMA N of a tensor-core block (two CTAs per SM)
 
 // Per-block descriptor (one CTA).
 struct BjBlock {

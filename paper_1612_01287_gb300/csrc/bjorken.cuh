@@ -72,6 +72,9 @@ struct BjTcArgs {
   int* err;
 };
 
+// Largest MMA N (state columns per block) of the tensor-core stage kernel.
+constexpr int kTcMaxCols = 80;
+
 cudaError_t bj_tc_set_attributes();
 size_t bj_tc_smem_bytes(int nc, int R);
 cudaError_t bj_tc_stage_launch(const BjTcArgs& a, int nblocks, size_t smem, cudaStream_t st);

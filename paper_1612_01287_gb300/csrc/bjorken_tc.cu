@@ -38,6 +38,7 @@ constexpr int kTcThreads = 128;
 constexpr uint32_t kATile = 128 * 128;  // bytes: 128 rows x 32 FP32
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kErrTimeout = 97;
+constexpr int kTcMaxRowsPerWarp = 20;  // MMA N <= 80: state rows per warp in a K-block
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -272,33 +273,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
   }
 
   // ---- main loop over K-blocks of 32 rows j' ----
+  // The state rows of K-block it+1 are loaded into registers while K-block it
+  // is split and multiplied; every thread checks for itself that the MMAs
+  // that last read a B buffer are done before overwriting it, so one CTA
+  // barrier per K-block suffices.
   const float* Fblk = a.Fin + blk.soff;
+  float bv[kTcMaxRowsPerWarp];
+  auto load_b = [&](int it) {
+    const int jj = it * 32 + lane;
+#pragma unroll
+    for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
+      const int c = warp + 4 * u;
+      bv[u] = (c < ncv && jj < Q) ? Fblk[(size_t)c * Q + jj] : 0.f;
+    }
+  };
+  load_b(0);
   bool aborted = false;
+  int lost = 0;
   for (int it = 0; it < nkb; ++it) {
     const int s = it & 1;
     const uint32_t par = (uint32_t)(it >> 1) & 1u;
-    const int jj = it * 32 + lane;
-    // state rows c = warp, warp + 4, ...: 8 loads in flight per thread
-    for (int c0 = warp; c0 < NC; c0 += 32) {
-      float v[8];
+    // B buffer s was last read by the MMAs of it-2
+    if (it >= 2 && !mbar_wait(&done[s], (uint32_t)((it - 2) >> 1) & 1u)) lost = 1;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int c = c0 + 4 * u;
-        v[u] = (c < ncv && jj < Q) ? Fblk[(size_t)c * Q + jj] : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int c = c0 + 4 * u;
-        if (c < NC) {
-          const float hi = tf32_rn(v[u]);
-          const uint32_t o = swz(c, lane);
-          *reinterpret_cast<float*>(Bhi(s) + o) = hi;
-          *reinterpret_cast<float*>(Blo(s) + o) = v[u] - hi;
-        }
+    for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
+      const int c = warp + 4 * u;
+      if (c < NC) {
+        const float hi = tf32_rn(bv[u]);
+        const uint32_t o = swz(c, lane);
+        *reinterpret_cast<float*>(Bhi(s) + o) = hi;
+        *reinterpret_cast<float*>(Blo(s) + o) = bv[u] - hi;
       }
     }
+    if (it + 1 < nkb) load_b(it + 1);
     // K^P tile of this K-block: wait for the bulk copy, split in place
-    const int copy_lost = !mbar_wait(&full[s], par);
+    if (!mbar_wait(&full[s], par)) lost = 1;
     {
       float4* ah = reinterpret_cast<float4*>(Ahi(s));
       float4* al = reinterpret_cast<float4*>(Alo(s));
@@ -310,12 +319,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
       }
     }
     fence_proxy_async();
-    if (__syncthreads_or(copy_lost)) {
+    if (__syncthreads_or(lost)) {
       if (tid == 0) tc_report(a.err, kErrTimeout, blk.first);
       aborted = true;
       break;
     }
-    int mma_lost = 0;
     if (tid == 0) {
       tc_fence_after();
 #pragma unroll
@@ -329,29 +337,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
       mma_commit(&done[s]);
       last_commit = it;
       if (it + 1 < nkb) {
-        // buffer (it+1)&1 was last read by the MMAs of it-1
-        bool ok = true;
-        if (it >= 1) ok = mbar_wait(&done[(it - 1) & 1], (uint32_t)((it - 1) >> 1) & 1u);
-        if (ok) {
+        // A buffer (it+1)&1 was last read by the MMAs of it-1
+        if (it == 0 || mbar_wait(&done[(it - 1) & 1], (uint32_t)((it - 1) >> 1) & 1u)) {
           mbar_expect_tx(&full[(it + 1) & 1], abytes);
           bulk_g2s(Ahi((it + 1) & 1), Asrc + (size_t)(it + 1) * rows * 32, abytes,
                    &full[(it + 1) & 1]);
           last_copy = it + 1;
         } else {
-          tc_report(a.err, kErrTimeout, blk.first);
-          mma_lost = 1;
+          lost = 1;  // reported at the next barrier
         }
       }
-    }
-    if (__syncthreads_or(mma_lost)) {
-      aborted = true;
-      break;
     }
   }
 
   // all MMAs done (commits complete in issue order); the outcome is made
   // uniform across the CTA before anyone branches on it
-  int lost = aborted ? 1 : !mbar_wait(&done[(nkb - 1) & 1], (uint32_t)((nkb - 1) >> 1) & 1u);
+  lost = aborted ? 1 : !mbar_wait(&done[(nkb - 1) & 1], (uint32_t)((nkb - 1) >> 1) & 1u);
   if (__syncthreads_or(lost)) {
     if (tid == 0 && !aborted) tc_report(a.err, kErrTimeout, blk.first);
     // bounded wait for what thread 0 issued, then release tensor memory

@@ -1,6 +1,9 @@
 // host.cu -- C ABI of the R-SLB library (include/rslb.h): argument checks,
 // FP64 quadrature generation, velocity tables, device buffers and launches.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -746,6 +749,17 @@ cudaError_t batch_enqueue(rslb_sod_batch* b, int nsteps) {
   return cudaSuccess;
 }
 
+// Tuning results of this process: (device, FP64, V, Q_L, N_Omega + 1) ->
+// (tile cells, CTAs per SM).
+struct TuneKey {
+  int dev, fp64, V, QL, nm;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, fp64, V, QL, nm) < std::tie(o.dev, o.fp64, o.V, o.QL, o.nm);
+  }
+};
+std::map<TuneKey, std::pair<int, int>> g_tune;
+std::mutex g_tune_mu;
+
 template <typename T>
 int batch_build_classes(rslb_sod_batch* b, int autotune) {
   // runs grouped by (V, nm); each group's runs sorted by decreasing step count
@@ -798,9 +812,21 @@ int batch_build_classes(rslb_sod_batch* b, int autotune) {
     if (cudaMalloc(&c.runs_dev, sizeof(SodRunDesc<T>) * rd.size()) != cudaSuccess)
       return set_error(RSLB_ERR_ALLOC, "rslb_sod_batch_init: cudaMalloc failed");
     cudaMemcpy(c.runs_dev, rd.data(), sizeof(SodRunDesc<T>) * rd.size(), cudaMemcpyHostToDevice);
-    // candidate tile kernels for this V (the automatic choice first)
-    std::vector<int> cands = {c.B};
+    // candidate tile kernels for this V (the automatic choice first); a
+    // choice already timed in this process for the same device, precision
+    // and velocity set is reused
+    const TuneKey key{dev, b->fp64 ? 1 : 0, V, QL, nm};
+    int cachedB = 0, cachedK = 0;
     if (autotune) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        cachedB = it->second.first;
+        cachedK = it->second.second;
+      }
+    }
+    std::vector<int> cands = {cachedB ? cachedB : c.B};
+    if (autotune && !cachedB) {
       const int alt[] = {28, 32, 16, 8};
       for (int B : alt)
         if (B != c.B && sod_stage_smem_bytes(b->fp64, B, V, QL, nm) > 0 &&
@@ -818,9 +844,10 @@ int batch_build_classes(rslb_sod_batch* b, int autotune) {
       cudaMemcpy(td, tasks.data(), sizeof(SodTask) * tasks.size(), cudaMemcpyHostToDevice);
       const size_t smem = sod_stage_smem_bytes(b->fp64, B, V, QL, nm);
       const int maxk = (smem * 2 + 4096 <= (size_t)max_smem + 1024) ? 2 : 1;
-      for (int k = 1; k <= (autotune ? maxk : 1); ++k) {
+      const bool timing = autotune && !cachedB;
+      for (int k = 1; k <= (timing ? maxk : 1); ++k) {
         float ms = 0.f;
-        if (autotune) {
+        if (timing) {
           cudaEvent_t e0, e1;
           cudaEventCreate(&e0);
           cudaEventCreate(&e1);
@@ -837,13 +864,17 @@ int batch_build_classes(rslb_sod_batch* b, int autotune) {
           cudaEventDestroy(e0);
           cudaEventDestroy(e1);
         }
-        if (!autotune || ms < best) {
+        if (!timing || ms < best) {
           best = ms;
           bestB = B;
-          bestK = k;
+          bestK = cachedB ? cachedK : k;
         }
       }
       cudaFree(td);
+    }
+    if (autotune && !cachedB) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = {bestB, bestK};
     }
     c.B = bestB;
     c.ctas_per_sm = bestK;

@@ -148,4 +148,28 @@ __device__ __forceinline__ void aeq_node(T t, T wt, T A, T sh2, T uinv, bool at_
   }
 }
 
+// One level of a transposing warp reduction of 32 compensated (hi, lo)
+// values per lane: lanes with bit OFF set keep the upper half of their
+// values, exchange the other half with lane ^ OFF and add with an
+// error-free TwoSum, so after the levels 16, 8, 4, 2, 1 lane l holds the
+// warp total of value l in h[0] + lo[0].
+template <int OFF>
+__device__ __forceinline__ void tr_level(float (&h)[32], float (&lo)[32], int lane) {
+  const bool up = (lane & OFF) != 0;
+#pragma unroll
+  for (int i = 0; i < OFF; ++i) {
+    const float sh = up ? h[i] : h[i + OFF];
+    const float sl = up ? lo[i] : lo[i + OFF];
+    const float kh = up ? h[i + OFF] : h[i];
+    const float kl = up ? lo[i + OFF] : lo[i];
+    const float rh = __shfl_xor_sync(0xffffffffu, sh, OFF);
+    const float rl = __shfl_xor_sync(0xffffffffu, sl, OFF);
+    const float t = kh + rh;
+    const float bp = t - kh;
+    const float e = (kh - (t - bp)) + (rh - bp);
+    h[i] = t;
+    lo[i] = (kl + rl) + e;
+  }
+}
+
 }  // namespace rslb

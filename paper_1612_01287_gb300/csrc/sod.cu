@@ -349,13 +349,41 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
 #pragma unroll
           for (int q = 0; q < 5; ++q) acc[c][q].add(blk[c][q]);
       }
+      if constexpr (sizeof(T) == 4) {
+        // FP32 transposing reduction of the compensated pairs (sum, -c):
+        // lane l ends with value l; only hi + lo is formed in FP64
+        static_assert(VN * 5 <= 32, "moment values per warp");
+        float h[32], lo[32];
 #pragma unroll
-      for (int c = 0; c < VN; ++c)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          const double s = warp_sum(acc[c][q].value());
-          if (lane == 0) msum[q * B + warp * VN + c] = s;
+        for (int i = 0; i < 32; ++i) {
+          h[i] = 0.f;
+          lo[i] = 0.f;
         }
+#pragma unroll
+        for (int c = 0; c < VN; ++c)
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            h[c * 5 + q] = acc[c][q].s;
+            lo[c * 5 + q] = -acc[c][q].c;
+          }
+        tr_level<16>(h, lo, lane);
+        tr_level<8>(h, lo, lane);
+        tr_level<4>(h, lo, lane);
+        tr_level<2>(h, lo, lane);
+        tr_level<1>(h, lo, lane);
+        if (lane < VN * 5) {
+          const int c = lane / 5, q = lane - 5 * (lane / 5);
+          msum[q * B + warp * VN + c] = (double)h[0] + (double)lo[0];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < VN; ++c)
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const double s = warp_sum(acc[c][q].value());
+            if (lane == 0) msum[q * B + warp * VN + c] = s;
+          }
+      }
     }
     __syncthreads();
 
@@ -368,22 +396,39 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
       if (!Lo.ok) {
         if (s0 + c < g.Z) report_error(err, 6, s0 + c);
         Lo.n = 1.0; Lo.T = 1.0; Lo.beta = 0.0; Lo.gamma = 1.0; Lo.u = 0.0;
-      } else {
-        double tau = g.tau;
-        if (g.tau_mode == kTauEtas)
-          tau = g.tau_AW0 / Lo.T *
-                (1.0 - 0.25 * log(Lo.n / (Lo.T * Lo.T * Lo.T) * g.lambda_ref));
+      } else if (g.tau_mode == kTauEtas) {
+        const double tau = g.tau_AW0 / Lo.T *
+                           (1.0 - 0.25 * log(Lo.n / (Lo.T * Lo.T * Lo.T) * g.lambda_ref));
         g0 = Lo.gamma / tau;
         g1 = Lo.gamma * Lo.beta / tau;
+      } else if constexpr (sizeof(T) == 4) {
+        const float itau = 1.f / float(g.tau);
+        g0 = float(Lo.gamma) * itau;
+        g1 = float(Lo.gamma * Lo.beta) * itau;
+      } else {
+        g0 = Lo.gamma / g.tau;
+        g1 = Lo.gamma * Lo.beta / g.tau;
       }
-      const double A = asinh(Lo.u);
-      const double sh = sinh(0.5 * A);
-      cell[0 * B + c] = Lo.n;
-      cell[1 * B + c] = Lo.T;
-      cell[2 * B + c] = Lo.u;
-      cell[3 * B + c] = A;
-      cell[4 * B + c] = (Lo.u > 0.0) ? A / Lo.u : 1.0;
-      cell[5 * B + c] = 2.0 * sh * sh;
+      if constexpr (sizeof(T) == 4) {
+        // FP32 from here on: the coefficients are computed in FP32
+        const float u = float(Lo.u);
+        const float A = asinhf(u);
+        cell[0 * B + c] = Lo.n;
+        cell[1 * B + c] = Lo.T;
+        cell[2 * B + c] = u;
+        cell[3 * B + c] = A;
+        cell[4 * B + c] = (u > 0.f) ? A / u : 1.f;
+        cell[5 * B + c] = u * u / (float(Lo.gamma) + 1.f);  // 2 sinh^2(A/2) = gamma - 1
+      } else {
+        const double A = asinh(Lo.u);
+        const double sh = sinh(0.5 * A);
+        cell[0 * B + c] = Lo.n;
+        cell[1 * B + c] = Lo.T;
+        cell[2 * B + c] = Lo.u;
+        cell[3 * B + c] = A;
+        cell[4 * B + c] = (Lo.u > 0.0) ? A / Lo.u : 1.0;
+        cell[5 * B + c] = 2.0 * sh * sh;
+      }
       cell[6 * B + c] = (Lo.beta < 0.0) ? -1.0 : 1.0;
       cell[7 * B + c] = Lo.ok ? 1.0 : 0.0;
       gco[2 * c] = T(g0);

@@ -4,12 +4,21 @@
 // A CTA owns 28 output cells, split into two halves of 14; one thread walks a
 // velocity row and advances both halves in lock-step, the left half in the x
 // lane and the right half in the y lane of float2 values, so every arithmetic
-// instruction of the sweep does two cells.  Shared-memory rows are stored as
-// 22 float2 "slots": slot s holds (cell s0-4+s, cell s0+10+s), i.e. each half
-// with its own 4-cell halo on each side.  The rest of the stage -- moments
-// (Kahan-compensated FP32, FP64 combination), FP64 Landau matching, the f^eq
-// coefficients, WENO5 in difference form, relaxation, RK update -- follows
-// the scalar kernel of sod.cu.
+// instruction of the sweep does two cells.  Shared memory holds the 36 cells
+// s0-4 .. s0+31 of every velocity row densely (row pitch 144 B, so 16-byte
+// accesses of 8 consecutive rows hit distinct banks); "slot" s of the sweep
+// is the pair (position s, position s+14).  Interior tiles are brought in by
+// tensor-memory-access bulk copies (cp.async.bulk.tensor, one box per block
+// of rows, completion on an mbarrier), boundary tiles by plain loads.  The
+// rest of the stage -- moments (Kahan-compensated FP32 with an error-free
+// FP32 warp reduction), FP64 Landau matching, the f^eq coefficients, WENO5 in
+// difference form, relaxation, RK update -- follows the scalar kernel of
+// sod.cu.
+#include <cuda.h>
+
+#include <cstring>
+#include <mutex>
+
 #include "rslb_device.cuh"
 #include "sod.cuh"
 
@@ -18,10 +27,11 @@ namespace {
 
 constexpr int kH = 14;          // cells per half
 constexpr int kB2 = 2 * kH;     // output cells per CTA
-constexpr int kS = kH + 8;      // float2 slots per row (4-cell halo per side)
-constexpr int kP = 2 * kS;      // floats per row: 44 = 11 x 16 B (odd count)
+constexpr int kC = kB2 + 8;     // cells staged per row: 36
+constexpr int kP = kC;          // floats per row: 36 (144 B)
 constexpr int kNT = 224;        // 7 warps: one per two-slot chunk in the moments
 constexpr int kMP = 8;          // coefficient pitch (m) for N_Omega <= 7
+constexpr int kInflight = 8;    // 16-byte global loads in flight per thread (staging, store)
 
 __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -38,12 +48,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 __device__ __forceinline__ void report_err(int* err, int code, int cell) {
   if (atomicCAS(err, 0, code) == 0) err[1] = cell;
-}
-
-__device__ __forceinline__ double warp_sum_d(double x) {
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-  return x;
 }
 
 // WENO5 correction (omega . g) of sod.cu::weno_corr for two faces at once,
@@ -79,6 +83,15 @@ __device__ __forceinline__ void ld2slots(const float* p, float2* out) {
   out[1] = make_float2(v.z, v.w);
 }
 
+// Slots s, s+1 (s even) of a dense row: x from positions s, s+1, y from
+// positions s+14, s+15.
+__device__ __forceinline__ void ld_slot_pair(const float* row, int s, float2* out) {
+  const float2 a = *reinterpret_cast<const float2*>(row + s);
+  const float2 b = *reinterpret_cast<const float2*>(row + s + kH);
+  out[0] = make_float2(a.x, b.x);
+  out[1] = make_float2(a.y, b.y);
+}
+
 template <bool POS>
 __device__ __forceinline__ float2 face_corr2(const float2* J, int wc) {
   const float2 k13 = splat(13.f / 12.f);
@@ -96,7 +109,11 @@ __device__ __forceinline__ float2 face_corr2(const float2* J, int wc) {
 }
 
 // Sweep a whole row (both halves): slots 4..17 are the outputs; window of
-// 10 slots [i-4, i+6) around the current two-slot chunk i.
+// 10 slots [i-4, i+6) around the current two-slot chunk i.  Results go back
+// into the row in place: the left-half outputs (positions 4..17) and the
+// right-half outputs of slots >= 8 (positions >= 22) are never read again by
+// the sweep; the right-half outputs of slots 4..7 (positions 18..21) are held
+// until the left half has read those positions (slots 18..21).
 template <bool POS>
 __device__ __forceinline__ void sweep_row2(float* row, float xi, const float2* wp2, int nm,
                                            const float* __restrict__ ck,
@@ -106,8 +123,9 @@ __device__ __forceinline__ void sweep_row2(float* row, float xi, const float2* w
   const float2 xi2 = splat(xi);
   const float2 sixth = splat(1.f / 6.f);
   float2 R[NW], J[NW];
+  float2 held[2];
 #pragma unroll
-  for (int c = 0; c < NW; c += 2) ld2slots(row + 2 * c, R + c);
+  for (int c = 0; c < NW; c += 2) ld_slot_pair(row, c, R + c);
 #pragma unroll
   for (int c = 0; c < NW; ++c) J[c] = mul2(xi2, R[c]);
   float2 Cl = face_corr2<POS>(J, 3);
@@ -148,95 +166,158 @@ __device__ __forceinline__ void sweep_row2(float* row, float xi, const float2* w
         J[c] = J[c + 2];
         R[c] = R[c + 2];
       }
-      ld2slots(row + 2 * (i + 6), R + NW - 2);  // slots i+6, i+7
+      ld_slot_pair(row, i + 6, R + NW - 2);  // slots i+6, i+7
       J[NW - 2] = mul2(xi2, R[NW - 2]);
       J[NW - 1] = mul2(xi2, R[NW - 1]);
     }
-    *reinterpret_cast<float4*>(row + 2 * i) = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
+    *reinterpret_cast<float2*>(row + i) = make_float2(out[0].x, out[1].x);
+    if (t < 2) {
+      held[t] = make_float2(out[0].y, out[1].y);
+    } else {
+      *reinterpret_cast<float2*>(row + i + kH) = make_float2(out[0].y, out[1].y);
+    }
+    if (t == 5) {  // slots 20, 21 have just been read
+      *reinterpret_cast<float2*>(row + 4 + kH) = held[0];
+      *reinterpret_cast<float2*>(row + 6 + kH) = held[1];
+    }
   }
+}
+
+__device__ __forceinline__ int tma_box_rows_dev(int V, int* nbox) {
+  const int nb = (V + 255) / 256;
+  int r = (V + nb - 1) / nb;
+  r = (r + 7) / 8 * 8;
+  *nbox = nb;
+  return r;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
 }  // namespace
 
-// Shared memory: tile [V][kP] floats, then partial moments, cell scalars,
-// coefficients [QL][kH][kMP][2] floats and gco [kH][4] floats.
+// Shared memory: tile [rows][kP] floats (rows = V rounded up to whole TMA
+// boxes), then partial moments, cell scalars, coefficients
+// [QL][kH][kMP][2] floats, gco [kH][4] floats and an mbarrier.
+static int tma_box_rows(int V, int* nbox) {
+  const int nb = (V + 255) / 256;
+  int r = (V + nb - 1) / nb;
+  r = (r + 7) / 8 * 8;  // a box is 144 r bytes: a multiple of 128 B
+  if (nbox) *nbox = nb;
+  return r;
+}
+
+static size_t tile_rows(int V) {
+  int nb = 0;
+  const int r = tma_box_rows(V, &nb);
+  return (size_t)nb * r;
+}
+
 size_t sod32_smem_bytes(int V, int QL) {
-  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
-  return al(sizeof(float) * (size_t)V * kP) + al(sizeof(double) * 5 * kB2) +
+  auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
+  return al(sizeof(float) * tile_rows(V) * kP) + al(sizeof(double) * 5 * kB2) +
          al(sizeof(double) * 8 * kB2) + al(sizeof(float) * (size_t)QL * kH * kMP * 2) +
-         al(sizeof(float) * kH * 4);
+         al(sizeof(float) * kH * 4) + 128 + 128;
 }
 
 // One stage of one tile starting at cell s0 (the whole CTA).
 __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
                                            const float* __restrict__ fn, float* fout, int stage,
                                            int* err, const SodGeom& g, const SodTables<float>& tb,
-                                           const int* __restrict__ rowv, int nneg, int s0) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+                                           const int* __restrict__ rowv, int nneg, int s0,
+                                           const CUtensorMap* tmap, int box_rows, int nbox,
+                                           uint32_t phase) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
   const int V = g.V;
-  float* tile = reinterpret_cast<float*>(smem_raw);
-  double* msum = reinterpret_cast<double*>(smem_raw + al(sizeof(float) * (size_t)V * kP));
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float* tile = reinterpret_cast<float*>(base);
+  const size_t tile_bytes = al(sizeof(float) * (size_t)nbox * box_rows * kP);
+  double* msum = reinterpret_cast<double*>(base + tile_bytes);
   double* cell = msum + 5 * kB2;
-  float* coef = reinterpret_cast<float*>(cell + 8 * kB2);  // [QL][kH][kMP][2]
-  float* gco = coef + (size_t)g.QL * kH * kMP * 2;         // [kH][g0x g0y g1x g1y]
+  float* coef = reinterpret_cast<float*>(
+      base + tile_bytes + al(sizeof(double) * 5 * kB2) + al(sizeof(double) * 8 * kB2));
+  float* gco = coef + (size_t)g.QL * kH * kMP * 2;  // [kH][g0x g0y g1x g1y]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(
+      reinterpret_cast<unsigned char*>(gco) + al(sizeof(float) * kH * 4));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // ---- 1. stage rows: cell c (relative to s0-4, 0 <= c < 36) goes to slot c
-  //         (x, left half) if c < 22 and to slot c-14 (y, right half) if c >= 14 ----
+  // ---- 1. stage rows: cell s0-4+p goes to position p (0 <= p < 36) ----
   const bool interior = (s0 - 4 >= 0) && (s0 + kB2 + 4 <= g.Z);
-  if (interior) {
-    // four 16-byte loads in flight per thread before any shared-memory store
+  if (interior && tmap) {
+    // one thread issues the box copies; everyone waits on the mbarrier
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const uint32_t bytes = (uint32_t)(nbox * box_rows * kP * sizeof(float));
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                   "r"(bytes)
+                   : "memory");
+      for (int b = 0; b < nbox; ++b)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(tile + (size_t)b * box_rows * kP)),
+            "l"(tmap), "r"(s0 - 4), "r"(b * box_rows), "r"(smem_u32(bar))
+            : "memory");
+    }
+    __syncthreads();  // the barrier is initialised before anyone polls it
+    uint32_t ok = 0;
+    for (int it = 0; it < (1 << 22) && !ok; ++it) {
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(ok)
+          : "r"(smem_u32(bar)), "r"(phase)
+          : "memory");
+      if (!ok && it > 32) __nanosleep(32);
+    }
+    if (!ok && tid == 0) report_err(err, 97, s0);
+  } else if (interior) {
+    // eight 16-byte loads in flight per thread before the shared-memory stores
     const float* src = fin + s0 - 4;
-    for (int base = tid; base < V * 9; base += 4 * kNT) {
-      float4 x[4];
+    for (int base_i = tid; base_i < V * 9; base_i += kInflight * kNT) {
+      float4 x[kInflight];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int idx = base + u * kNT;
+      for (int u = 0; u < kInflight; ++u) {
+        const int idx = base_i + u * kNT;
         if (idx < V * 9) {
           const int v = idx / 9, q = idx - v * 9;
           x[u] = __ldg(reinterpret_cast<const float4*>(src + (size_t)v * g.ldz + 4 * q));
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int idx = base + u * kNT;
+      for (int u = 0; u < kInflight; ++u) {
+        const int idx = base_i + u * kNT;
         if (idx < V * 9) {
           const int v = idx / 9, q = idx - v * 9;
-          float* row = tile + v * kP;
-          const float e[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const int c = 4 * q + w;
-            if (c < kS) row[2 * c] = e[w];
-            if (c >= kH) row[2 * (c - kH) + 1] = e[w];
-          }
+          *reinterpret_cast<float4*>(tile + v * kP + 4 * q) = x[u];
         }
       }
     }
   } else {
-    for (int idx = tid; idx < V * 36; idx += kNT) {
-      const int v = idx / 36, c = idx - v * 36;
-      const int s = s0 - 4 + c;
+    for (int idx = tid; idx < V * kC; idx += kNT) {
+      const int v = idx / kC, c = idx - v * kC;
+      const int sc = s0 - 4 + c;
       float val;
-      if (s >= 0 && s < g.Z) val = fin[(size_t)v * g.ldz + s];
+      if (sc >= 0 && sc < g.Z) val = fin[(size_t)v * g.ldz + sc];
       else if (g.bc == kBcPeriodic) {
-        int sp = s % g.Z;
+        int sp = sc % g.Z;
         if (sp < 0) sp += g.Z;
         val = fin[(size_t)v * g.ldz + sp];
-      } else if (g.bc == kBcOutflow) val = fin[(size_t)v * g.ldz + (s < 0 ? 0 : g.Z - 1)];
-      else val = s < 0 ? tb.ghostL[v] : tb.ghostR[v];
-      float* row = tile + v * kP;
-      if (c < kS) row[2 * c] = val;
-      if (c >= kH) row[2 * (c - kH) + 1] = val;
+      } else if (g.bc == kBcOutflow) val = fin[(size_t)v * g.ldz + (sc < 0 ? 0 : g.Z - 1)];
+      else val = sc < 0 ? tb.ghostL[v] : tb.ghostR[v];
+      tile[v * kP + c] = val;
     }
   }
   __syncthreads();
 
   const bool collide = g.tau_mode != kTauNone;
   if (collide) {
-    // ---- 2. moments: warp w owns slots 4+2w, 5+2w (4 cells), lanes own rows;
+    // ---- 2. moments: warp w owns cells 4w .. 4w+3 of the tile, lanes own rows;
     //         blocks of four rows, Kahan-compensated across blocks ----
     {
       float s[4][5], cpen[4][5];
@@ -254,7 +335,7 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
         for (int u = 0; u < 4; ++u) {
           const int v = v0 + 32 * u;
           if (v < V) {
-            const float4 x = *reinterpret_cast<const float4*>(tile + v * kP + 2 * (4 + 2 * warp));
+            const float4 x = *reinterpret_cast<const float4*>(tile + v * kP + 4 + 4 * warp);
             const float e[4] = {x.x, x.y, x.z, x.w};
             float w[5];
 #pragma unroll
@@ -275,61 +356,78 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
             s[c][q] = t;
           }
       }
-      // element e of the float4 is: slot 4+2w (x, y), slot 5+2w (x, y)
-      // x = left half cell 2w + {0,1}, y = right half cell 14 + 2w + {0,1}
+      // FP32 transposing reduction of the 20 (sum, -compensation) pairs; only
+      // the final hi + lo of each is formed in FP64
+      float h[32], lo[32];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int cellidx = (c & 1) ? kH + 2 * warp + (c >> 1) : 2 * warp + (c >> 1);
+      for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-          const double sum = warp_sum_d((double)s[c][q] - (double)cpen[c][q]);
-          if (lane == 0) msum[q * kB2 + cellidx] = sum;
+          h[c * 5 + q] = s[c][q];
+          lo[c * 5 + q] = -cpen[c][q];
         }
+#pragma unroll
+      for (int i = 20; i < 32; ++i) {
+        h[i] = 0.f;
+        lo[i] = 0.f;
+      }
+      tr_level<16>(h, lo, lane);
+      tr_level<8>(h, lo, lane);
+      tr_level<4>(h, lo, lane);
+      tr_level<2>(h, lo, lane);
+      tr_level<1>(h, lo, lane);
+      if (lane < 20) {
+        const int c = lane / 5, q = lane - 5 * (lane / 5);
+        msum[q * kB2 + 4 * warp + c] = (double)h[0] + (double)lo[0];
       }
     }
     __syncthreads();
 
-    // ---- 3a. Landau matching (FP64) and relaxation time, one thread per cell ----
+    // ---- 3a. Landau matching (FP64) and relaxation time, one thread per cell;
+    //          what the f^eq coefficients need is passed on in FP32 ----
+    float* cellf = reinterpret_cast<float*>(cell);  // [8][kB2]
     if (tid < kB2) {
       const int c = tid;
       LandauOut Lo = landau_factored(msum[c], msum[kB2 + c], msum[2 * kB2 + c],
                                      msum[3 * kB2 + c], msum[4 * kB2 + c]);
-      double g0 = 0.0, g1 = 0.0;
+      float g0 = 0.f, g1 = 0.f;
       if (!Lo.ok) {
         if (s0 + c < g.Z) report_err(err, 6, s0 + c);
         Lo.n = 1.0; Lo.T = 1.0; Lo.beta = 0.0; Lo.gamma = 1.0; Lo.u = 0.0;
+      } else if (g.tau_mode == kTauEtas) {
+        const double tau = g.tau_AW0 / Lo.T *
+                           (1.0 - 0.25 * log(Lo.n / (Lo.T * Lo.T * Lo.T) * g.lambda_ref));
+        g0 = float(Lo.gamma / tau);
+        g1 = float(Lo.gamma * Lo.beta / tau);
       } else {
-        double tau = g.tau;
-        if (g.tau_mode == kTauEtas)
-          tau = g.tau_AW0 / Lo.T *
-                (1.0 - 0.25 * log(Lo.n / (Lo.T * Lo.T * Lo.T) * g.lambda_ref));
-        g0 = Lo.gamma / tau;
-        g1 = Lo.gamma * Lo.beta / tau;
+        const float itau = 1.f / float(g.tau);
+        g0 = float(Lo.gamma) * itau;
+        g1 = float(Lo.gamma * Lo.beta) * itau;
       }
-      const double A = asinh(Lo.u);
-      const double sh = sinh(0.5 * A);
-      cell[0 * kB2 + c] = Lo.n;
-      cell[1 * kB2 + c] = Lo.T;
-      cell[2 * kB2 + c] = Lo.u;
-      cell[3 * kB2 + c] = A;
-      cell[4 * kB2 + c] = (Lo.u > 0.0) ? A / Lo.u : 1.0;
-      cell[5 * kB2 + c] = 2.0 * sh * sh;
-      cell[6 * kB2 + c] = (Lo.beta < 0.0) ? -1.0 : 1.0;
-      cell[7 * kB2 + c] = Lo.ok ? 1.0 : 0.0;
+      const float u = float(Lo.u);
+      const float A = asinhf(u);
+      cellf[0 * kB2 + c] = float(Lo.n);
+      cellf[1 * kB2 + c] = float(Lo.T);
+      cellf[2 * kB2 + c] = u;
+      cellf[3 * kB2 + c] = A;
+      cellf[4 * kB2 + c] = (u > 0.f) ? A / u : 1.f;
+      cellf[5 * kB2 + c] = u * u / (float(Lo.gamma) + 1.f);  // 2 sinh^2(A/2) = gamma - 1
+      cellf[6 * kB2 + c] = (Lo.beta < 0.0) ? -1.f : 1.f;
+      cellf[7 * kB2 + c] = Lo.ok ? 1.f : 0.f;
       // gco[i][g0x g0y g1x g1y], cell c = half h, index i
       const int h = c / kH, i = c - h * kH;
-      gco[4 * i + h] = float(g0);
-      gco[4 * i + 2 + h] = float(g1);
+      gco[4 * i + h] = g0;
+      gco[4 * i + 2 + h] = g1;
     }
     __syncthreads();
 
     // ---- 3b. f^eq coefficients: 8 threads per cell share the 32 nodes ----
     {
       const int c = tid >> 3, q = tid & 7;  // 28 cells x 8 = 224 threads
-      const double ud = cell[2 * kB2 + c];
-      const float A = float(cell[3 * kB2 + c]), sh2 = float(cell[5 * kB2 + c]);
-      const float uinv = (ud > 0.0) ? float(1.0 / ud) : 0.f;
-      const bool at_rest = !(ud > 0.0);
+      const float ud = cellf[2 * kB2 + c];
+      const float A = cellf[3 * kB2 + c], sh2 = cellf[5 * kB2 + c];
+      const float uinv = (ud > 0.f) ? 1.f / ud : 0.f;
+      const bool at_rest = !(ud > 0.f);
       float J3[kMaxM], J4[kMaxM];
 #pragma unroll
       for (int m = 0; m < kMaxM; ++m) { J3[m] = 0.f; J4[m] = 0.f; }
@@ -346,9 +444,9 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
             J4[m] += __shfl_xor_sync(0xffffffffu, J4[m], o);
           }
       if (q == 0) {
-        const float fac = float(cell[7 * kB2 + c] * cell[0 * kB2 + c] * cell[4 * kB2 + c] * 0.25);
-        const float theta = float(cell[1 * kB2 + c]);
-        const float sgn = float(cell[6 * kB2 + c]);
+        const float fac = cellf[7 * kB2 + c] * cellf[0 * kB2 + c] * cellf[4 * kB2 + c] * 0.25f;
+        const float theta = cellf[1 * kB2 + c];
+        const float sgn = cellf[6 * kB2 + c];
         const int h = c / kH, i = c - h * kH;
         float sm = fac;
 #pragma unroll
@@ -386,54 +484,45 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
   }
   __syncthreads();
 
-  // ---- 5. store: cell c of the tile = slot 4 + (c mod 14), half c / 14 ----
+  // ---- 5. store: cell c of the tile is position 4 + c ----
   const float a = (stage == 1) ? 0.75f : 1.f / 3.f;
   const float b = (stage == 1) ? 0.25f : 2.f / 3.f;
   if (s0 + kB2 <= g.Z) {
-    // full tile: 7 chunks of 4 cells per row, 16-byte global accesses, four
-    // loads of f_n in flight per thread
-    for (int base = tid; base < V * 7; base += 4 * kNT) {
-      float4 fo[4];
+    // full tile: 7 chunks of 4 cells per row, 16-byte accesses, eight loads
+    // of f_n in flight per thread
+    for (int base_i = tid; base_i < V * 7; base_i += kInflight * kNT) {
+      float4 fo[kInflight];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int idx = base + u * kNT;
+      for (int u = 0; u < kInflight; ++u) {
+        const int idx = base_i + u * kNT;
         if (stage != 0 && idx < V * 7) {
           const int v = idx / 7, q = idx - v * 7;
           fo[u] = __ldg(reinterpret_cast<const float4*>(fn + (size_t)v * g.ldz + s0 + 4 * q));
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int idx = base + u * kNT;
+      for (int u = 0; u < kInflight; ++u) {
+        const int idx = base_i + u * kNT;
         if (idx < V * 7) {
           const int v = idx / 7, q = idx - v * 7;
-          const float* row = tile + v * kP;
-          float r[4];
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const int c = 4 * q + w;
-            const int h = c >= kH, i = c - h * kH;
-            r[w] = row[2 * (4 + i) + h];
-          }
+          float4 r = *reinterpret_cast<const float4*>(tile + v * kP + 4 + 4 * q);
           if (stage != 0) {
-            r[0] = a * fo[u].x + b * r[0];
-            r[1] = a * fo[u].y + b * r[1];
-            r[2] = a * fo[u].z + b * r[2];
-            r[3] = a * fo[u].w + b * r[3];
+            r.x = a * fo[u].x + b * r.x;
+            r.y = a * fo[u].y + b * r.y;
+            r.z = a * fo[u].z + b * r.z;
+            r.w = a * fo[u].w + b * r.w;
           }
-          *reinterpret_cast<float4*>(fout + (size_t)v * g.ldz + s0 + 4 * q) =
-              make_float4(r[0], r[1], r[2], r[3]);
+          *reinterpret_cast<float4*>(fout + (size_t)v * g.ldz + s0 + 4 * q) = r;
         }
       }
     }
   } else {
     for (int idx = tid; idx < V * kB2; idx += kNT) {
       const int v = idx / kB2, c = idx - v * kB2;
-      const int s = s0 + c;
-      if (s < g.Z) {
-        const int h = c / kH, i = c - h * kH;
-        const size_t o = (size_t)v * g.ldz + s;
-        float r = tile[v * kP + 2 * (4 + i) + h];
+      const int sc = s0 + c;
+      if (sc < g.Z) {
+        const size_t o = (size_t)v * g.ldz + sc;
+        float r = tile[v * kP + 4 + c];
         if (stage != 0) r = a * fn[o] + b * r;
         fout[o] = r;
       }
@@ -444,25 +533,71 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
 __global__ void __launch_bounds__(kNT, 2)
 sod32_stage_kernel(const float* __restrict__ fin, const float* __restrict__ fn, float* fout,
                    int stage, int* err, SodGeom g, SodTables<float> tb, const int* __restrict__ rowv,
-                   int nneg) {
-  sod32_tile(fin, fn, fout, stage, err, g, tb, rowv, nneg, blockIdx.x * kB2);
+                   int nneg, const __grid_constant__ CUtensorMap tmap, int use_tma, int box_rows,
+                   int nbox) {
+  sod32_tile(fin, fn, fout, stage, err, g, tb, rowv, nneg, blockIdx.x * kB2,
+             use_tma ? &tmap : nullptr, box_rows, nbox, 0u);
 }
 
-// Batched: a persistent grid walks the task list of all runs of one class.
+// Batched: a persistent grid walks the task list of all runs of one class
+// (plain-load staging).
 __global__ void __launch_bounds__(kNT, 2)
 sod32_batch_kernel(const SodRunDesc<float>* __restrict__ runs, const SodTask* __restrict__ tasks,
                    int ntasks, const long long* __restrict__ step, int stage, int* err) {
   const long long n = *step;
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const SodTask tk = tasks[t];
-    const SodRunDesc<float> R = runs[tk.run];
+    const SodRunDesc<float>& R = runs[tk.run];
     if (n >= R.nsteps) break;  // tasks are ordered by decreasing step count
     const float* fin = stage == 0 ? R.F0 : (stage == 1 ? R.F1 : R.F2);
     float* fout = stage == 0 ? R.F1 : (stage == 1 ? R.F2 : R.F0);
-    sod32_tile(fin, R.F0, fout, stage, err, R.g, R.tb, R.rowv, R.nneg, tk.s0);
+    int nbox = 0;
+    const int br = tma_box_rows_dev(R.g.V, &nbox);
+    sod32_tile(fin, R.F0, fout, stage, err, R.g, R.tb, R.rowv, R.nneg, tk.s0, nullptr, br, nbox,
+               0u);
     __syncthreads();
   }
 }
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+// Tensor map of one population buffer: 2-D FP32 [V][Z] with row stride ldz,
+// box 36 cells x box_rows rows, zero fill outside.
+bool make_map(CUtensorMap* m, const float* f, int Z, int ldz, int V, int box_rows) {
+  EncodeTiled enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)Z, (cuuint64_t)V};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldz * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kC, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(f), dims, strides, box,
+             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
 
 cudaError_t sod32_batch_launch(size_t smem, int grid, const SodRunDesc<float>* runs,
                                const SodTask* tasks, int ntasks, const long long* step, int stage,
@@ -484,14 +619,21 @@ cudaError_t sod32_stage_launch(const SodGeom& g, const SodTables<float>& tb, con
                                int* err, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sod32_stage_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e = sod32_set_attributes();
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  int nbox = 0;
+  const int br = tma_box_rows(g.V, &nbox);
+  CUtensorMap m;
+  std::memset(&m, 0, sizeof(m));
+  // TMA needs a 16-byte aligned base and row stride (cudaMalloc'd buffers,
+  // ldz a multiple of 32) and at least one whole interior tile
+  const bool tma = g.Z >= kB2 + 8 && (reinterpret_cast<uintptr_t>(fin) % 16) == 0 &&
+                   (g.ldz % 4) == 0 && make_map(&m, fin, g.Z, g.ldz, g.V, br);
   const int grid = (g.Z + kB2 - 1) / kB2;
-  sod32_stage_kernel<<<grid, kNT, sod32_smem_bytes(g.V, g.QL), st>>>(fin, fn, fout, stage, err, g,
-                                                                      tb, rowv, nneg);
+  sod32_stage_kernel<<<grid, kNT, sod32_smem_bytes(g.V, g.QL), st>>>(
+      fin, fn, fout, stage, err, g, tb, rowv, nneg, m, tma ? 1 : 0, br, nbox);
   return cudaGetLastError();
 }
 

@@ -128,3 +128,18 @@ def test_batch_rejects_bad_runs():
         SodBatch([dict(Z=0, Q_xi=8, tau=0.1, t_end=0.1)])
     with pytest.raises(RslbError):
         SodBatch([dict(Z=10, Q_xi=8, tau=-1.0, t_end=0.1)])
+
+
+def test_tuning_is_cached_per_velocity_set():
+    """A second batch with the same velocity sets reuses the first one's
+    choice (tile kernel, CTAs per SM) without timing again."""
+    import time
+    from paper_1612_01287_gb300 import SodBatch
+    runs = [dict(Z=600, Q_xi=50, tau=0.1, t_end=0.01), dict(Z=300, Q_xi=8, tau=0.1, t_end=0.01)]
+    with SodBatch(runs, precision="f32", autotune=True) as b:
+        first = b.tuning()
+    t0 = time.perf_counter()
+    with SodBatch(runs[::-1], precision="f32", autotune=True) as b:
+        second = b.tuning()
+    assert first == second
+    assert time.perf_counter() - t0 < 30
