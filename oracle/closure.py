@@ -24,6 +24,10 @@ Definitions (velocity index v = k * Q + j, radial node k, polar node j):
   quadrature-weighted sense,
       delta' = delta - W Phi (Phi^T W Phi)^{-1} Phi^T delta,  W = diag(w_j w_k),
   so that sum_v delta'_v phi_v = 0 (N^t, T^tt, T^tz unchanged).
+* Positivity limiter: the conserving correction of a cell is scaled by
+  alpha = min(1, min over v with f_v > 0 and delta'_v < 0 of
+  LIMIT_THETA f_v / (-delta'_v)), so no positive population loses more than
+  half of itself in one step; the scaling keeps sum_v delta'_v phi_v = 0.
 * Loss: L = sum over samples and outputs of (y - t)^2 / (n_samples * n_out).
 
 Flat parameter layout: W1 [H][D] row-major, b1 [H], W2 [H][H], b2 [H],
@@ -154,13 +158,26 @@ def project(delta, Q, QL):
     return delta - (c @ Phi.T) * W
 
 
+LIMIT_THETA = 0.5
+
+
+def limit(delta, f):
+    """Scale each cell's correction so positive populations stay positive."""
+    alpha = np.ones(delta.shape[0])
+    for s in range(delta.shape[0]):
+        m = (f[s] > 0) & (delta[s] < 0)
+        if m.any():
+            alpha[s] = min(1.0, float(np.min(LIMIT_THETA * f[s][m] / -delta[s][m])))
+    return delta * alpha[:, None]
+
+
 def correction(theta, f_lo, tau, Q, QL, H):
-    """The conserving correction delta' [Z][V] of every cell."""
+    """The conserving, limited correction delta' [Z][V] of every cell."""
     V = Q * QL
     X = features(f_lo, tau)
     y, _ = forward(theta, X, 3 * V + 1, H, V)
     n = f_lo.sum(1)
-    return project(n[:, None] * y, Q, QL)
+    return limit(project(n[:, None] * y, Q, QL), f_lo)
 
 
 def bf16_round(x):

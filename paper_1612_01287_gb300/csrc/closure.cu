@@ -12,7 +12,9 @@
 //    (FP32 master copy for Adam), FP32 biases and accumulation;
 //  * correction delta = n_s * y, minus its component along the collision
 //    invariants (1, p, p xi) in the quadrature-weighted sense, so the cell's
-//    N^t, T^tt and T^tz are unchanged.
+//    N^t, T^tt and T^tz are unchanged; the result is scaled down where it
+//    would take more than half of a positive population (a positivity
+//    limiter that keeps the conservation).
 //
 // Training: one CTA holds up to 128 samples; each thread runs forward and
 // backward for its sample out of shared memory, then the CTA reduces the
@@ -36,6 +38,7 @@ namespace {
 constexpr int kMaxD = 128;
 constexpr int kMaxO = 32;
 constexpr int kSmemLimit = 232448;
+constexpr float kLimitTheta = 0.5f;  // positivity limiter of the correction
 
 struct MlpShape {
   int D, H, O;
@@ -411,7 +414,15 @@ __global__ void __launch_bounds__(128) closure_apply_kernel(MlpShape s, const fl
   mlp_forward<H, false>(s, sw, x, h1, h2, nullptr, nullptr,
                         [&](int o, float y) { delta[o] = n * y; });
   project_add(cc, V, delta, corr);
-  for (int v = 0; v < V; ++v) fout[(size_t)v * ldz + c] = fin[(size_t)v * ldz + c] + corr[v];
+  // positivity limiter: scale the (conserving) correction so that no
+  // positive population loses more than kLimitTheta of itself
+  float alpha = 1.f;
+  for (int v = 0; v < V; ++v) {
+    const float f = fin[(size_t)v * ldz + c];
+    if (f > 0.f && corr[v] < 0.f) alpha = fminf(alpha, kLimitTheta * f / -corr[v]);
+  }
+  for (int v = 0; v < V; ++v)
+    fout[(size_t)v * ldz + c] = fin[(size_t)v * ldz + c] + alpha * corr[v];
 }
 
 // Restriction, thread per cell: f_lo[k*Ql + i] = sum_j R[i][j] f_hi[k*Qh + j].

@@ -128,3 +128,22 @@ def test_bf16_rounding():
     assert r[2] == 1.0 + 2 ** -7
     assert r[3] == -2.5
     assert abs(r[4] - 3.140625) < 1e-12
+
+
+def test_limiter_keeps_positive_populations_and_invariants():
+    Q, QL, H = 8, 3, 16
+    V = Q * QL
+    rng = np.random.default_rng(4)
+    theta = rng.normal(0, 3.0, size=sum(C.param_sizes(3 * V + 1, H, V)))  # large corrections
+    f = np.stack([oracle.feq(Q, QL, 5, 0.5 + 0.1 * s, 1.0, 0.05 * s) for s in range(6)])
+    d = C.correction(theta, f, 0.01, Q, QL, H)
+    g = f + d
+    pos = f > 0
+    assert np.all(g[pos] >= (1 - C.LIMIT_THETA) * f[pos] - 1e-15)
+    Phi, _ = C.invariants(Q, QL)
+    assert np.abs(d @ Phi).max() < 1e-12
+    # the limiter never amplifies: |delta'| <= |projected delta|
+    X = C.features(f, 0.01)
+    y, _ = C.forward(theta, X, 3 * V + 1, H, V)
+    raw = C.project(f.sum(1)[:, None] * y, Q, QL)
+    assert np.all(np.abs(d) <= np.abs(raw) + 1e-15)
