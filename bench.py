@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--no-side", action="store_true",
                     help="skip the batched Bjorken and batched shock-tube side measurements")
     ap.add_argument("--bj-steps", type=int, default=20)
+    ap.add_argument("--bj-runs", type=int, default=16384,
+                    help="runs of the batched Bjorken side measurement")
+    ap.add_argument("--bj-modes", default="simt,tf32x3",
+                    help="contraction modes of the batched Bjorken side measurement")
+    ap.add_argument("--only", choices=["bjorken", "sod_batch", "closure"],
+                    help="run just this side measurement and print its JSON (profiling)")
     ap.add_argument("--batch-steps", type=int, default=10)
     return ap.parse_args()
 
@@ -183,12 +189,12 @@ def bench_bjorken(stream, steps=None):
     (nondimensional tau from 1), dtau = 1e-3.  One step = one RK3 step of every run."""
     from paper_1612_01287_gb300 import Bjorken
     steps = steps or ARGS.bj_steps
-    qxi, eta_s, T0 = workloads.bjorken_batch()
+    qxi, eta_s, T0 = workloads.bjorken_batch(nruns=ARGS.bj_runs)
     taus = 5 * HBARC_GEV_FM * eta_s / (0.5 * T0)
     cv = 3 * int(qxi.sum())
     flops = 3 * 2 * 3 * float((qxi.astype(np.float64) ** 2).sum())  # K^P contraction only
     out = {"runs": len(qxi), "cv_per_step": cv, "kp_flops_per_step": flops}
-    for mode in ("simt", "tf32x3"):
+    for mode in ARGS.bj_modes.split(","):
         with Bjorken(qxi, "parton", taus, Q_L=3, precision="f32", kp_mode=mode, dtau=1e-3,
                      stream=stream) as b:
             b.step(1)
@@ -229,9 +235,9 @@ def bench_sod_batch(stream, steps=None):
 def bench_closure(stream):
     """Learned closure (Q_xi = 8 + MLP) against the plain high-order method
     (Q_xi = 200).  Accuracy: shock tube on 2048 cells to t = 0.2, trained on
-    ~1e6 cell samples of Q_xi = 200 runs with tau in {0.03, 0.1, 0.3, 1, 3},
-    judged at tau in {0.1, 0.5 (not trained on), 1}.  Speed: per-step time of
-    each path on the 65536-cell tube."""
+    ~1e6 cell samples of Q_xi = 200 runs with 8 tau log-spaced in [1e-3, 10],
+    judged at tau in {0.01, 0.1, 0.5, 1} (none of them trained on).  Speed:
+    per-step time of each path on the 65536-cell tube."""
     import torch
     from paper_1612_01287_gb300 import MLP, Sod, closure_sample, closure_step
     QL, QHI, QLO = 3, 200, 8
@@ -243,10 +249,10 @@ def bench_closure(stream):
     kw = dict(Z=Z, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", dt=dt, stream=stream)
     t0 = time.perf_counter()
     Xs, Ts = [], []
-    for tau in (0.03, 0.1, 0.3, 1.0, 3.0):
+    for tau in np.logspace(-3.0, 1.0, 8):
         with Sod(Q_xi=QHI, tau=tau, **kw) as hi, Sod(Q_xi=QLO, tau=tau, **kw) as lo:
-            for n in range(0, nsteps, 4):
-                hi.step(3)
+            for n in range(0, nsteps, 8):
+                hi.step(7)
                 X = torch.empty((Z, D), device="cuda")
                 T = torch.empty((Z, V), device="cuda")
                 closure_sample(hi, lo, tau, X.data_ptr(), T.data_ptr())
@@ -264,12 +270,13 @@ def bench_closure(stream):
            "steps": nsteps, "network": "73-64-64-24 SiLU, BF16 weights, FP32 accumulate"}
     with MLP(D, 64, V, seed=20161201, stream=stream) as m:
         t0 = time.perf_counter()
-        losses = m.train(X.data_ptr(), T.data_ptr(), X.shape[0], epochs=12, batch=8192, lr=2e-3,
+        m.fit_normalization(X.data_ptr(), T.data_ptr(), X.shape[0])
+        losses = m.train(X.data_ptr(), T.data_ptr(), X.shape[0], epochs=40, batch=8192, lr=2e-3,
                          seed=2)
         out["train_s"] = time.perf_counter() - t0
         out["loss_first_last"] = [float(losses[0]), float(losses[-1])]
         acc = {}
-        for tau in (0.1, 0.5, 1.0):
+        for tau in (0.01, 0.1, 0.5, 1.0):
             try:
                 with Sod(Q_xi=QHI, tau=tau, **kw) as hi, Sod(Q_xi=QLO, tau=tau, **kw) as lo, \
                         Sod(Q_xi=QLO, tau=tau, **kw) as cl:
@@ -291,6 +298,7 @@ def bench_closure(stream):
                 acc[str(tau)] = {"error": repr(exc)[:200]}
         out["l2_vs_q200"] = acc
         theta = m.get_params()
+        norm = m.get_normalization()
     # per-step cost at 65536 cells: the network is evaluated in every cell;
     # its output layer is zeroed here so the (untrained-for-this-dt) correction
     # does not perturb the tube -- the work per step is the same
@@ -303,6 +311,7 @@ def bench_closure(stream):
         th = theta.copy()
         th[D * 64 + 64 + 64 * 64 + 64:] = 0.0
         mz.set_params(th)
+        mz.set_normalization(*norm)
         hi.step(2)
         closure_step(cl, mz, 1.0, 2)
         ms_hi = _timed(stream, hi.step, 8) / 8
@@ -480,7 +489,9 @@ def run_ours(args, rank, world, local_rank):
                     "note": "one tube, FP64 everywhere; bound by the FP64 pipe, not HBM"}
 
     B_tile = tubes[0].launch_info()[0]
-    kname = "sod32_stage_kernel" if B_tile == 28 else "sod_stage_kernel<float,%d>" % B_tile
+    from paper_1612_01287_gb300._lib import PACKED_TILE_CELLS
+    kname = ("sod32_stage_kernel" if B_tile == PACKED_TILE_CELLS
+             else "sod_stage_kernel<float,%d>" % B_tile)
     for t in tubes:
         t.close()
     extras = {}
@@ -536,6 +547,17 @@ def main():
     args = parse()
     ARGS = args
     rank, world, local_rank = dist_env()
+    if args.only:
+        import torch
+        from paper_1612_01287_gb300 import build
+        build.build()
+        torch.cuda.set_device(local_rank)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        fn = {"bjorken": bench_bjorken, "sod_batch": bench_sod_batch,
+              "closure": bench_closure}[args.only]
+        print(json.dumps({args.only: fn(stream)}), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_ours(args, rank, world, local_rank)

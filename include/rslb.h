@@ -54,6 +54,9 @@ extern "C" {
 #define RSLB_F32 0 /* populations, fluxes, relaxation in FP32; Landau in FP64 */
 #define RSLB_F64 1 /* everything in FP64 */
 
+/* Cells per CTA tile of the packed FP32x2 shock-tube stage kernel. */
+#define RSLB_PACKED_TILE_CELLS 28
+
 #define RSLB_BC_FIXED_EQ 0 /* ghost cells = left/right equilibria (Sec. IV A) */
 #define RSLB_BC_OUTFLOW 1  /* ghost cells = first/last interior cell */
 #define RSLB_BC_PERIODIC 2 /* periodic domain */
@@ -114,8 +117,9 @@ typedef struct rslb_config {
   const double* n0;
   const double* T0;
   const double* beta0;
-  /* Cells per CTA tile of the stage kernel: 0 = automatic; otherwise 28 (the
-   * packed FP32x2 kernel: V >= 128, N_Omega <= 7), 32 or 16 (RSLB_F32), 16 or
+  /* Cells per CTA tile of the stage kernel: 0 = automatic; otherwise
+   * RSLB_PACKED_TILE_CELLS (the packed FP32x2 kernel: V >= 128,
+   * N_Omega <= 7), 32 or 16 (RSLB_F32), 16 or
    * 8 (RSLB_F64).  A tuning knob; results agree to rounding. */
   int tile_cells;
 } rslb_config;
@@ -175,7 +179,8 @@ int rslb_set_state(rslb_handle* h, const void* f, int on_device);
 /* Simulation time and step count of the handle (host-side bookkeeping). */
 int rslb_time(const rslb_handle* h, double* t, long long* steps);
 
-/* The stage kernel the handle launches: cells per CTA tile (28 = packed
+/* The stage kernel the handle launches: cells per CTA tile
+ * (RSLB_PACKED_TILE_CELLS = packed
  * FP32x2 kernel) and threads per CTA.  Errors: RSLB_ERR_ARG. */
 int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* threads);
 
@@ -401,12 +406,28 @@ int rslb_mlp_num_params(const rslb_mlp* m);
 int rslb_mlp_get_params(rslb_mlp* m, float* theta);
 int rslb_mlp_set_params(rslb_mlp* m, const float* theta);
 
-/* Y [n][n_out] = net(X [n][n_in]); device pointers; asynchronous. */
+/*
+ * Fixed (not trained) normalisation: the network sees (x - mu) * inv_sd and
+ * its output is multiplied by out_sd (identity after rslb_mlp_create).
+ * set/get: caller-owned host arrays of n_in, n_in and n_out floats.
+ * fit: from training data on the device (X [n][n_in], T [n][n_out]): mu and
+ * 1/sd = the column means and inverse standard deviations of X, out_sd = the
+ * column root-mean-squares of T (1 for constant or zero columns);
+ * synchronises.
+ */
+int rslb_mlp_set_normalization(rslb_mlp* m, const float* mu, const float* inv_sd,
+                               const float* out_sd);
+int rslb_mlp_get_normalization(rslb_mlp* m, float* mu, float* inv_sd, float* out_sd);
+int rslb_mlp_fit_normalization(rslb_mlp* m, const float* X, const float* T, int n);
+
+/* Y [n][n_out] = out_sd * net((X [n][n_in] - mu) * inv_sd); device pointers;
+ * asynchronous. */
 int rslb_mlp_forward(rslb_mlp* m, const float* X, int n, float* Y);
 
 /*
- * Mean-squared loss L = sum (y - t)^2 / (n n_out) over the n samples
- * (X [n][n_in], T [n][n_out], device) and its gradient with respect to the
+ * Mean-squared loss L = sum (y - t / out_sd)^2 / (n n_out) over the n
+ * samples, y = net((x - mu) * inv_sd) the network in normalised units
+ * (X [n][n_in], T [n][n_out], device), and its gradient with respect to the
  * parameters, by the library's backward kernels (weights as used in the
  * forward pass, i.e. BF16-rounded).  loss: host; grad: host, or NULL.
  * Synchronises.
@@ -434,8 +455,9 @@ int rslb_restrict(rslb_handle* hi, rslb_handle* lo);
 
 /*
  * One training sample per cell: lo := R(hi); X [Z][3V+1] (device) = features
- * of lo (populations of cells s-1, s, s+1 over n_s, then log10 tau, outflow
- * copies at the ends); then both handles advance one RK3 step and
+ * of lo (over n_s: the populations of cell s, f_{s+1} - f_s, f_s - f_{s-1};
+ * then log10 tau; outflow copies at the ends); then both handles advance one
+ * RK3 step and
  * T [Z][V] (device) = P(R(hi) - lo) / n_s with P the projection that removes
  * the components along the collision invariants (1, p, p xi) weighted by
  * w_j w_k.  V = Q_L Q_xi(lo) <= 32.  Synchronises.
@@ -443,8 +465,10 @@ int rslb_restrict(rslb_handle* hi, rslb_handle* lo);
 int rslb_closure_sample(rslb_handle* hi, rslb_handle* lo, double tau, float* X, float* T);
 
 /*
- * nsteps RK3 steps of `lo`, each followed by f += P(n_s net(features)) in
- * every cell.  The network must be (3V+1) -> V.  Asynchronous.
+ * nsteps RK3 steps of `lo`, each followed in every cell by f += alpha
+ * P(n_s net(features)), alpha <= 1 the largest factor that leaves every
+ * positive population at least half of itself.  The network must be
+ * (3V+1) -> V.  Asynchronous.
  */
 int rslb_closure_step(rslb_handle* lo, rslb_mlp* m, double tau, int nsteps);
 

@@ -14,12 +14,17 @@ Definitions (velocity index v = k * Q + j, radial node k, polar node j):
   Gauss-Legendre exactness (degree <= 2 Q_lo - 1) makes the low-order
   populations reproduce F_{m,k} for every m < Q_lo, in particular the
   moments N^mu and T^{mu nu} (m <= 2, Eq. macro_jk).
-* Features of cell s: the low-order populations of cells s-1, s, s+1
-  (outflow copies at the ends) divided by n_s = sum_v f_{v,s}, then
-  log10(tau): 3 V + 1 numbers.
+* Features of cell s (outflow copies at the ends), all divided by
+  n_s = sum_v f_{v,s}: the populations of cell s, the forward differences
+  f_{s+1} - f_s and the backward differences f_s - f_{s-1}, then log10(tau):
+  3 V + 1 numbers.
 * MLP: h1 = silu(W1 x + b1), h2 = silu(W2 h1 + b2), y = W3 h2 + b3 with
   silu(a) = a / (1 + e^{-a}).
-* Correction of cell s: delta = n_s y, made conserving by removing its
+* Normalisation (fixed, not trained): the network sees (x - mu) * inv_sd and
+  its output is multiplied by out_sd; fit_normalization takes mu, sd as the
+  column means and standard deviations of the training inputs and out_sd as
+  the column root-mean-squares of the targets (1 where a column is constant).
+* Correction of cell s: delta = n_s out_sd * y, made conserving by removing its
   component along the collision invariants phi = (1, p_k, p_k xi_j) in the
   quadrature-weighted sense,
       delta' = delta - W Phi (Phi^T W Phi)^{-1} Phi^T delta,  W = diag(w_j w_k),
@@ -130,8 +135,31 @@ def features(f_lo, tau):
     n = f_lo.sum(1)
     left = np.vstack([f_lo[:1], f_lo[:-1]])
     right = np.vstack([f_lo[1:], f_lo[-1:]])
-    X = np.hstack([left, f_lo, right]) / n[:, None]
+    X = np.hstack([f_lo, right - f_lo, f_lo - left]) / n[:, None]
     return np.hstack([X, np.full((Z, 1), np.log10(tau))])
+
+
+def identity_norm(D, O):
+    return np.zeros(D), np.ones(D), np.ones(O)
+
+
+def fit_normalization(X, T):
+    """(mu, inv_sd, out_sd) from training inputs X [N][D] and targets T [N][O]."""
+    X = np.asarray(X, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    mu = X.mean(0)
+    sd = np.sqrt(((X - mu) ** 2).mean(0))
+    inv_sd = np.where(sd > 0, 1.0 / np.where(sd > 0, sd, 1.0), 1.0)
+    rms = np.sqrt((T * T).mean(0))
+    out_sd = np.where(rms > 0, rms, 1.0)
+    return mu, inv_sd, out_sd
+
+
+def net(theta, X, D, H, O, norm=None):
+    """The normalised network: out_sd * MLP((X - mu) * inv_sd)."""
+    mu, inv_sd, out_sd = norm if norm is not None else identity_norm(D, O)
+    y, _ = forward(theta, (np.asarray(X) - mu) * inv_sd, D, H, O)
+    return y * out_sd
 
 
 def invariants(Q, QL, T0=1.0):
@@ -171,11 +199,11 @@ def limit(delta, f):
     return delta * alpha[:, None]
 
 
-def correction(theta, f_lo, tau, Q, QL, H):
+def correction(theta, f_lo, tau, Q, QL, H, norm=None):
     """The conserving, limited correction delta' [Z][V] of every cell."""
     V = Q * QL
     X = features(f_lo, tau)
-    y, _ = forward(theta, X, 3 * V + 1, H, V)
+    y = net(theta, X, 3 * V + 1, H, V, norm)
     n = f_lo.sum(1)
     return limit(project(n[:, None] * y, Q, QL), f_lo)
 

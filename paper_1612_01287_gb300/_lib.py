@@ -18,6 +18,7 @@ OK = 0
 ERR = {1: "RSLB_ERR_ARG", 2: "RSLB_ERR_CFL", 3: "RSLB_ERR_STIFF", 4: "RSLB_ERR_ALLOC",
        5: "RSLB_ERR_CUDA", 6: "RSLB_ERR_NONPHYSICAL", 7: "RSLB_ERR_UNSUPPORTED"}
 F32, F64 = 0, 1
+PACKED_TILE_CELLS = 28  # RSLB_PACKED_TILE_CELLS
 BC = {"fixed_eq": 0, "outflow": 1, "periodic": 2}
 TAU = {"const": 0, "etas": 1, "none": 2}
 
@@ -474,6 +475,9 @@ def _mlp_sigs(L):
         "rslb_mlp_get_params": (i, [p, p]),
         "rslb_mlp_set_params": (i, [p, p]),
         "rslb_mlp_forward": (i, [p, p, i, p]),
+        "rslb_mlp_set_normalization": (i, [p, p, p, p]),
+        "rslb_mlp_get_normalization": (i, [p, p, p, p]),
+        "rslb_mlp_fit_normalization": (i, [p, p, p, i]),
         "rslb_mlp_loss_grad": (i, [p, p, p, i, ctypes.POINTER(d), p]),
         "rslb_mlp_train": (i, [p, p, p, i, i, i, d, u64, p]),
         "rslb_mlp_destroy": (None, [p]),
@@ -509,6 +513,20 @@ class MLP:
         t = np.ascontiguousarray(theta, dtype=np.float32)
         assert t.size == self.num_params
         _check(load().rslb_mlp_set_params(self._h, _ptr(t)))
+
+    def set_normalization(self, mu, inv_sd, out_sd):
+        a = [np.ascontiguousarray(x, dtype=np.float32) for x in (mu, inv_sd, out_sd)]
+        _check(load().rslb_mlp_set_normalization(self._h, *(_ptr(x) for x in a)))
+
+    def get_normalization(self):
+        a = [np.zeros(self.n_in, np.float32), np.zeros(self.n_in, np.float32),
+             np.zeros(self.n_out, np.float32)]
+        _check(load().rslb_mlp_get_normalization(self._h, *(_ptr(x) for x in a)))
+        return tuple(a)
+
+    def fit_normalization(self, X_ptr, T_ptr, n):
+        _check(load().rslb_mlp_fit_normalization(self._h, ctypes.c_void_p(X_ptr),
+                                                 ctypes.c_void_p(T_ptr), int(n)))
 
     def forward(self, X_ptr, n, Y_ptr):
         _check(load().rslb_mlp_forward(self._h, ctypes.c_void_p(X_ptr), int(n),

@@ -6,11 +6,12 @@
 //  * restriction R: high-order populations -> low-order ones, per radial
 //    node, through the Legendre moments m < Q_lo (exact for m <= 2, so the
 //    moments of Eq. macro_jk are preserved);
-//  * features of cell s: low-order populations of cells s-1, s, s+1 divided
-//    by n_s = sum_v f_{v,s}, then log10(tau);
+//  * features of cell s, over n_s = sum_v f_{v,s}: the low-order populations
+//    of cell s, f_{s+1} - f_s and f_s - f_{s-1}; then log10(tau);
 //  * MLP D -> H -> H -> O with SiLU after the hidden layers, BF16 weights
-//    (FP32 master copy for Adam), FP32 biases and accumulation;
-//  * correction delta = n_s * y, minus its component along the collision
+//    (FP32 master copy for Adam), FP32 biases and accumulation, behind a
+//    fixed input/output normalisation fitted to the training data;
+//  * correction delta = n_s * out_sd * y, minus its component along the collision
 //    invariants (1, p, p xi) in the quadrature-weighted sense, so the cell's
 //    N^t, T^tt and T^tz are unchanged; the result is scaled down where it
 //    would take more than half of a positive population (a positivity
@@ -61,13 +62,21 @@ MlpShape make_shape(int D, int H, int O) {
 }
 
 // Shared-memory weight block: W1T [D][H], W2 [H][H], W3 [O][H] (BF16 values
-// widened to FP32), b1 [H], b2 [H], b3 [O].
+// widened to FP32), b1 [H], b2 [H], b3 [O], then the fixed normalisation
+// mu [D], inv_sd [D], out_sd [O] (the network sees (x - mu) * inv_sd, its
+// output is scaled by out_sd).
 __host__ __device__ inline int wblock_floats(const MlpShape& s) {
+  return s.D * s.H + s.H * s.H + s.O * s.H + 2 * s.H + s.O + 2 * s.D + s.O;
+}
+
+__host__ __device__ inline int norm_offset(const MlpShape& s) {
   return s.D * s.H + s.H * s.H + s.O * s.H + 2 * s.H + s.O;
 }
 
 __device__ inline void load_weights(const MlpShape& s, const __nv_bfloat16* __restrict__ wb,
-                                    const float* __restrict__ theta, float* sw) {
+                                    const float* __restrict__ theta,
+                                    const float* __restrict__ nrm, float* sw) {
+  for (int e = threadIdx.x; e < 2 * s.D + s.O; e += blockDim.x) sw[norm_offset(s) + e] = nrm[e];
   float* W1T = sw;
   float* W2 = W1T + s.D * s.H;
   float* W3 = W2 + s.H * s.H;
@@ -165,6 +174,7 @@ __device__ __forceinline__ void mlp_forward(const MlpShape& s, const float* __re
 template <int H>
 __global__ void __launch_bounds__(128) mlp_train_kernel(MlpShape s, const float* __restrict__ theta,
                                                         const __nv_bfloat16* __restrict__ wb,
+                                                        const float* __restrict__ nrm,
                                                         const float* __restrict__ X,
                                                         const float* __restrict__ T,
                                                         const int* __restrict__ perm, int n0,
@@ -178,15 +188,19 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(MlpShape s, const float*
   const int tid = threadIdx.x;
   const int base = blockIdx.x * NS;
   const int cnt = min(NS, nb - base);
-  load_weights(s, wb, theta, sw);
-  // stage the inputs of the CTA's samples (coalesced)
+  load_weights(s, wb, theta, nrm, sw);
+  __syncthreads();
+  const float* mu = sw + norm_offset(s);
+  const float* isd = mu + s.D;
+  const float* osd = isd + s.D;
+  // stage the normalised inputs of the CTA's samples (coalesced)
   for (int e = tid; e < NS * s.D; e += NS) {
     const int r = e / s.D, c = e - r * s.D;
     float v = 0.f;
     if (r < cnt) {
       const int n = n0 + base + r;
       const int src = perm ? perm[n] : n;
-      v = X[(size_t)src * s.D + c];
+      v = (X[(size_t)src * s.D + c] - mu[c]) * isd[c];
     }
     act[r * pitch + c] = v;
   }
@@ -206,7 +220,7 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(MlpShape s, const float*
     // silu'(a1) and silu'(a2) go to the ga1 and ga2 slots, overwritten below
     mlp_forward<H, true>(s, sw, [&](int d) { return row[d]; }, h1, h2, rg1, rg2,
                          [&](int o, float y) {
-                           const float r = y - t[o];
+                           const float r = y - t[o] / osd[o];
                            sq += (double)r * r;
                            rgy[o] = 2.f * r * inv_norm;
                          });
@@ -339,6 +353,7 @@ __global__ void mlp_round_kernel(const float* __restrict__ theta, int P, __nv_bf
 template <int H>
 __global__ void __launch_bounds__(128) mlp_infer_kernel(MlpShape s, const float* __restrict__ theta,
                                                         const __nv_bfloat16* __restrict__ wb,
+                                                        const float* __restrict__ nrm,
                                                         const float* __restrict__ X, int n,
                                                         int pitch, float* Y) {
   extern __shared__ __align__(16) float smem_f[];
@@ -347,10 +362,14 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(MlpShape s, const float*
   const int tid = threadIdx.x, NS = blockDim.x;
   const int base = blockIdx.x * NS;
   const int cnt = min(NS, n - base);
-  load_weights(s, wb, theta, sw);
+  load_weights(s, wb, theta, nrm, sw);
+  __syncthreads();
+  const float* mu = sw + norm_offset(s);
+  const float* isd = mu + s.D;
+  const float* osd = isd + s.D;
   for (int e = tid; e < NS * s.D; e += NS) {
     const int r = e / s.D, c = e - r * s.D;
-    xs[r * pitch + c] = r < cnt ? X[(size_t)(base + r) * s.D + c] : 0.f;
+    xs[r * pitch + c] = r < cnt ? (X[(size_t)(base + r) * s.D + c] - mu[c]) * isd[c] : 0.f;
   }
   __syncthreads();
   if (tid >= cnt) return;
@@ -358,7 +377,7 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(MlpShape s, const float*
   float h1[H], h2[H];
   float* y = Y + (size_t)(base + tid) * s.O;
   mlp_forward<H, false>(s, sw, [&](int d) { return row[d]; }, h1, h2, nullptr, nullptr,
-                        [&](int o, float v) { y[o] = v; });
+                        [&](int o, float v) { y[o] = v * osd[o]; });
 }
 
 // ---------------------------------------------------------------------------
@@ -389,12 +408,13 @@ __device__ __forceinline__ void project_add(const ClosureConsts& cc, int V, cons
 template <int H>
 __global__ void __launch_bounds__(128) closure_apply_kernel(MlpShape s, const float* __restrict__ theta,
                                                             const __nv_bfloat16* __restrict__ wb,
+                                                            const float* __restrict__ nrm,
                                                             const float* __restrict__ fin,
                                                             float* fout, int Z, int ldz,
                                                             float logtau, ClosureConsts cc) {
   extern __shared__ __align__(16) float smem_f[];
   float* sw = smem_f;
-  load_weights(s, wb, theta, sw);
+  load_weights(s, wb, theta, nrm, sw);
   __syncthreads();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= Z) return;
@@ -403,16 +423,27 @@ __global__ void __launch_bounds__(128) closure_apply_kernel(MlpShape s, const fl
   float n = 0.f;
   for (int v = 0; v < V; ++v) n += fin[(size_t)v * ldz + c];
   const float inv_n = 1.f / n;
+  const float* mu = sw + norm_offset(s);
+  const float* isd = mu + s.D;
+  const float* osd = isd + s.D;
+  // features: f_s, f_{s+1} - f_s, f_s - f_{s-1} (over n_s), log10 tau
   auto x = [&](int d) {
-    if (d >= 3 * V) return logtau;
-    const int blk = d / V, v = d - blk * V;
-    const int cc2 = blk == 0 ? cl : (blk == 1 ? c : cr);
-    return fin[(size_t)v * ldz + cc2] * inv_n;
+    float r;
+    if (d >= 3 * V) {
+      r = logtau;
+    } else {
+      const int blk = d / V, v = d - blk * V;
+      const float fc = fin[(size_t)v * ldz + c];
+      if (blk == 0) r = fc * inv_n;
+      else if (blk == 1) r = (fin[(size_t)v * ldz + cr] - fc) * inv_n;
+      else r = (fc - fin[(size_t)v * ldz + cl]) * inv_n;
+    }
+    return (r - mu[d]) * isd[d];
   };
   float h1[H], h2[H];
   float delta[kMaxO], corr[kMaxO];
   mlp_forward<H, false>(s, sw, x, h1, h2, nullptr, nullptr,
-                        [&](int o, float y) { delta[o] = n * y; });
+                        [&](int o, float y) { delta[o] = n * osd[o] * y; });
   project_add(cc, V, delta, corr);
   // positivity limiter: scale the (conserving) correction so that no
   // positive population loses more than kLimitTheta of itself
@@ -445,7 +476,8 @@ __global__ void restrict_kernel(const float* __restrict__ fh, int ldh, int Qh,
   }
 }
 
-// Features of the low-order state (rows of X) and n_s.
+// Features of the low-order state (rows of X) and n_s: f_s, f_{s+1} - f_s,
+// f_s - f_{s-1}, all over n_s, then log10 tau.
 __global__ void features_kernel(const float* __restrict__ f, int Z, int ldz, int V, float logtau,
                                 float* X, float* ns) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -457,9 +489,10 @@ __global__ void features_kernel(const float* __restrict__ f, int Z, int ldz, int
   const float inv = 1.f / n;
   float* row = X + (size_t)c * (3 * V + 1);
   for (int v = 0; v < V; ++v) {
-    row[v] = f[(size_t)v * ldz + cl] * inv;
-    row[V + v] = f[(size_t)v * ldz + c] * inv;
-    row[2 * V + v] = f[(size_t)v * ldz + cr] * inv;
+    const float fc = f[(size_t)v * ldz + c];
+    row[v] = fc * inv;
+    row[V + v] = (f[(size_t)v * ldz + cr] - fc) * inv;
+    row[2 * V + v] = (fc - f[(size_t)v * ldz + cl]) * inv;
   }
   row[3 * V] = logtau;
 }
@@ -480,6 +513,48 @@ __global__ void target_kernel(const float* __restrict__ fref, const float* __res
 // ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
+// Column statistics for the normalisation, one CTA per column (fixed-order
+// tree reductions in FP64, two passes for the variance): columns of X give
+// mu and 1/sd, columns of T give the root-mean-square (1 for constant or
+// zero columns).
+__global__ void fit_norm_kernel(const float* __restrict__ X, const float* __restrict__ T, int n,
+                                int D, int O, float* nrm) {
+  __shared__ double red[256];
+  const int col = blockIdx.x, tid = threadIdx.x;
+  const bool is_x = col < D;
+  const float* src = is_x ? X + col : T + (col - D);
+  const int stride = is_x ? D : O;
+  auto reduce = [&](double v) {
+    red[tid] = v;
+    __syncthreads();
+    for (int o = 128; o >= 1; o >>= 1) {
+      if (tid < o) red[tid] += red[tid + o];
+      __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+  };
+  double a = 0.0;
+  for (int r = tid; r < n; r += 256) a += (double)src[(size_t)r * stride];
+  const double mean = reduce(a) / n;
+  double b = 0.0;
+  for (int r = tid; r < n; r += 256) {
+    const double x = (double)src[(size_t)r * stride];
+    const double d = is_x ? x - mean : x;
+    b += d * d;
+  }
+  const double sd = sqrt(reduce(b) / n);
+  if (tid == 0) {
+    if (is_x) {
+      nrm[col] = (float)mean;
+      nrm[D + col] = sd > 0.0 ? (float)(1.0 / sd) : 1.f;
+    } else {
+      nrm[2 * D + (col - D)] = sd > 0.0 ? (float)sd : 1.f;
+    }
+  }
+}
+
 uint64_t splitmix(uint64_t& x) {
   uint64_t z = (x += 0x9E3779B97F4A7C15ull);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -533,6 +608,7 @@ using namespace rslb;
 struct rslb_mlp {
   MlpShape s;
   cudaStream_t stream;
+  float* norm;  // mu [D] | inv_sd [D] | out_sd [O]
   float* theta;
   __nv_bfloat16* wb;
   float* grad;
@@ -578,7 +654,8 @@ cudaError_t dispatch_h(int H, F f) {
 
 void mlp_free(rslb_mlp* m) {
   if (!m) return;
-  void* p[] = {m->theta, m->wb, m->grad, m->m, m->v, m->part, m->lossp, m->loss_acc, m->perm};
+  void* p[] = {m->theta, m->wb, m->grad, m->m, m->v, m->part, m->lossp, m->loss_acc, m->perm,
+               m->norm};
   for (void* x : p)
     if (x) cudaFree(x);
   delete m;
@@ -622,7 +699,8 @@ cudaError_t mlp_batch_grad(rslb_mlp* m, const float* X, const float* T, const in
   const size_t smem = train_smem(s, ns);
   cudaError_t e = dispatch_h(s.H, [&](auto Hc) {
     constexpr int H = decltype(Hc)::value;
-    mlp_train_kernel<H><<<nblk, ns, smem, m->stream>>>(s, m->theta, m->wb, X, T, perm, n0, nb,
+    mlp_train_kernel<H><<<nblk, ns, smem, m->stream>>>(s, m->theta, m->wb, m->norm, X, T, perm,
+                                                       n0, nb,
                                                        inv_norm, mlp_pitch(s), m->part, m->lossp);
     return cudaGetLastError();
   });
@@ -668,12 +746,17 @@ extern "C" int rslb_mlp_create(rslb_mlp** out, int n_in, int n_hidden, int n_out
             cudaMalloc((void**)&m->grad, sizeof(float) * P) == cudaSuccess &&
             cudaMalloc((void**)&m->m, sizeof(float) * P) == cudaSuccess &&
             cudaMalloc((void**)&m->v, sizeof(float) * P) == cudaSuccess &&
-            cudaMalloc((void**)&m->loss_acc, sizeof(double)) == cudaSuccess;
+            cudaMalloc((void**)&m->loss_acc, sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&m->norm, sizeof(float) * (2 * s.D + s.O)) == cudaSuccess;
   if (!ok) {
     mlp_free(m);
     return set_error(RSLB_ERR_ALLOC, "rslb_mlp_create: cudaMalloc failed");
   }
+  std::vector<float> nrm(2 * s.D + s.O, 1.f);
+  for (int d = 0; d < s.D; ++d) nrm[d] = 0.f;  // mu = 0, inv_sd = 1, out_sd = 1
   cudaError_t e = set_smem_attrs(m->s);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->norm, nrm.data(), sizeof(float) * nrm.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->theta, th.data(), sizeof(float) * P, cudaMemcpyHostToDevice, m->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->m, 0, sizeof(float) * P, m->stream);
@@ -719,6 +802,49 @@ extern "C" int rslb_mlp_set_params(rslb_mlp* m, const float* theta) {
   return e == cudaSuccess ? RSLB_OK : cuda_error(e, "rslb_mlp_set_params");
 }
 
+extern "C" int rslb_mlp_set_normalization(rslb_mlp* m, const float* mu, const float* inv_sd,
+                                          const float* out_sd) {
+  clear_error();
+  if (!m || !mu || !inv_sd || !out_sd)
+    return set_error(RSLB_ERR_ARG, "rslb_mlp_set_normalization: NULL argument");
+  const MlpShape& s = m->s;
+  std::vector<float> h(2 * s.D + s.O);
+  std::memcpy(h.data(), mu, sizeof(float) * s.D);
+  std::memcpy(h.data() + s.D, inv_sd, sizeof(float) * s.D);
+  std::memcpy(h.data() + 2 * s.D, out_sd, sizeof(float) * s.O);
+  cudaError_t e = cudaMemcpyAsync(m->norm, h.data(), sizeof(float) * h.size(),
+                                  cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  return e == cudaSuccess ? RSLB_OK : cuda_error(e, "rslb_mlp_set_normalization");
+}
+
+extern "C" int rslb_mlp_get_normalization(rslb_mlp* m, float* mu, float* inv_sd, float* out_sd) {
+  clear_error();
+  if (!m || !mu || !inv_sd || !out_sd)
+    return set_error(RSLB_ERR_ARG, "rslb_mlp_get_normalization: NULL argument");
+  const MlpShape& s = m->s;
+  std::vector<float> h(2 * s.D + s.O);
+  cudaError_t e = cudaMemcpyAsync(h.data(), m->norm, sizeof(float) * h.size(),
+                                  cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_error(e, "rslb_mlp_get_normalization");
+  std::memcpy(mu, h.data(), sizeof(float) * s.D);
+  std::memcpy(inv_sd, h.data() + s.D, sizeof(float) * s.D);
+  std::memcpy(out_sd, h.data() + 2 * s.D, sizeof(float) * s.O);
+  return RSLB_OK;
+}
+
+extern "C" int rslb_mlp_fit_normalization(rslb_mlp* m, const float* X, const float* T, int n) {
+  clear_error();
+  if (!m || !X || !T || n < 1)
+    return set_error(RSLB_ERR_ARG, "rslb_mlp_fit_normalization: bad arguments");
+  const MlpShape& s = m->s;
+  fit_norm_kernel<<<s.D + s.O, 256, 0, m->stream>>>(X, T, n, s.D, s.O, m->norm);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  return e == cudaSuccess ? RSLB_OK : cuda_error(e, "rslb_mlp_fit_normalization");
+}
+
 extern "C" int rslb_mlp_forward(rslb_mlp* m, const float* X, int n, float* Y) {
   clear_error();
   if (!m || !X || !Y || n < 0) return set_error(RSLB_ERR_ARG, "rslb_mlp_forward: bad arguments");
@@ -729,7 +855,8 @@ extern "C" int rslb_mlp_forward(rslb_mlp* m, const float* X, int n, float* Y) {
   const size_t smem = sizeof(float) * (size_t)(((wblock_floats(s) + 3) & ~3) + ns * pitch);
   cudaError_t e = dispatch_h(s.H, [&](auto Hc) {
     constexpr int H = decltype(Hc)::value;
-    mlp_infer_kernel<H><<<(n + ns - 1) / ns, ns, smem, m->stream>>>(s, m->theta, m->wb, X, n,
+    mlp_infer_kernel<H><<<(n + ns - 1) / ns, ns, smem, m->stream>>>(s, m->theta, m->wb, m->norm,
+                                                                    X, n,
                                                                     pitch, Y);
     return cudaGetLastError();
   });
@@ -925,7 +1052,7 @@ extern "C" int rslb_closure_step(rslb_handle* lo, rslb_mlp* m, double tau, int n
     if (rc) return rc;
     cudaError_t e = dispatch_h(s.H, [&](auto Hc) {
       constexpr int H = decltype(Hc)::value;
-      closure_apply_kernel<H><<<G, TB, smem, vl.stream>>>(s, m->theta, m->wb,
+      closure_apply_kernel<H><<<G, TB, smem, vl.stream>>>(s, m->theta, m->wb, m->norm,
                                                           (const float*)vl.F0, (float*)vl.F1,
                                                           vl.Z, vl.ldz, lt, cc);
       return cudaGetLastError();

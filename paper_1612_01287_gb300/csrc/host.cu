@@ -350,12 +350,13 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
   if (c.tile_cells != 0) {
     // explicit tile width (tuning): must be one the kernels are built for
     const bool okB = fp64 ? (c.tile_cells == 16 || c.tile_cells == 8)
-                          : (c.tile_cells == 28 || c.tile_cells == 32 || c.tile_cells == 16);
+                          : (c.tile_cells == kSod32Cells || c.tile_cells == 32 || c.tile_cells == 16);
     if (!okB)
       return set_error(RSLB_ERR_ARG, "rslb_init: tile_cells must be 0 or one of %s",
-                       fp64 ? "16, 8" : "28, 32, 16");
-    if (c.tile_cells == 28 && (V < 128 || nm > 8))
-      return set_error(RSLB_ERR_ARG, "rslb_init: tile_cells = 28 needs V >= 128 and N_Omega <= 7");
+                       fp64 ? "16, 8" : "the packed width, 32, 16");
+    if (c.tile_cells == kSod32Cells && (V < 128 || nm > 8))
+      return set_error(RSLB_ERR_ARG,
+                       "rslb_init: the packed tile width needs V >= 128 and N_Omega <= 7");
     L.B = c.tile_cells;
   }
   if (L.B == 0)
@@ -670,7 +671,7 @@ extern "C" int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* thre
   clear_error();
   if (!h) return set_error(RSLB_ERR_ARG, "rslb_launch_info: NULL handle");
   if (tile_cells) *tile_cells = h->launch.B;
-  if (threads) *threads = h->launch.B == 28 ? 224 : 320;
+  if (threads) *threads = h->launch.B == kSod32Cells ? kSod32Threads : 320;
   return RSLB_OK;
 }
 
@@ -827,11 +828,11 @@ int batch_build_classes(rslb_sod_batch* b, int autotune) {
     }
     std::vector<int> cands = {cachedB ? cachedB : c.B};
     if (autotune && !cachedB) {
-      const int alt[] = {28, 32, 16, 8};
+      const int alt[] = {kSod32Cells, 32, 16, 8};
       for (int B : alt)
         if (B != c.B && sod_stage_smem_bytes(b->fp64, B, V, QL, nm) > 0 &&
             sod_stage_smem_bytes(b->fp64, B, V, QL, nm) <= (size_t)max_smem &&
-            !(B == 28 && (V < 128 || nm > 8)))
+            !(B == kSod32Cells && (V < 128 || nm > 8)))
           cands.push_back(B);
     }
     float best = 1e30f;

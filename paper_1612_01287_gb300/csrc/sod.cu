@@ -615,7 +615,7 @@ SodLaunch sod_pick_launch(bool fp64, int V, int QL, int nm, int max_smem) {
   if (!fp64) {
     // packed FP32x2 kernel: whole rows per thread, so it needs enough rows to
     // fill a CTA, N_Omega <= 7, and two CTAs per SM
-    if (V >= 128 && nm <= 8 && sod32_smem_bytes(V, QL) <= half) return {28, 0};
+    if (V >= 128 && nm <= 8 && sod32_smem_bytes(V, QL) <= half) return {kSod32Cells, 0};
     const int n32 = pick_nseg(V, 32, 320, 4), n16 = pick_nseg(V, 16, 320, 4);
     if (smem_for<float, 32, 320>(V, QL, nm, n32) <= half) return {32, 0};
     if (smem_for<float, 16, 320>(V, QL, nm, n16) <= half) return {16, 0};
@@ -654,7 +654,7 @@ cudaError_t sod_stage_launch(const SodLaunch& L, const SodGeom& g, const SodTabl
                              const int* rowv, int nneg, const T* fin, const T* fn, T* fout,
                              int stage, int* err, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
-    if (L.B == 28) return sod32_stage_launch(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
+    if (L.B == kSod32Cells) return sod32_stage_launch(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
   }
   switch (L.B) {
     case 32:
@@ -680,7 +680,7 @@ template cudaError_t sod_stage_launch<double>(const SodLaunch&, const SodGeom&,
 
 size_t sod_stage_smem_bytes(bool fp64, int B, int V, int QL, int nm) {
   if (!fp64) {
-    if (B == 28) return sod32_smem_bytes(V, QL);
+    if (B == kSod32Cells) return sod32_smem_bytes(V, QL);
     if (B == 32) return smem_for<float, 32, 320>(V, QL, nm, pick_nseg(V, 32, 320, 4));
     if (B == 16) return smem_for<float, 16, 320>(V, QL, nm, pick_nseg(V, 16, 320, 4));
   } else {
@@ -701,7 +701,7 @@ cudaError_t sod_batch_stage_launch(int B, size_t smem, int grid, const SodRunDes
                                    int stage, int* err, int V, cudaStream_t st) {
   if (ntasks == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (B == 28) return sod32_batch_launch(smem, grid, runs, tasks, ntasks, step, stage, err, st);
+    if (B == kSod32Cells) return sod32_batch_launch(smem, grid, runs, tasks, ntasks, step, stage, err, st);
     if (B == 32) {
       sod_batch_kernel<T, 32, 320><<<grid, 320, smem, st>>>(runs, tasks, ntasks, step, stage, err,
                                                            pick_nseg(V, 32, 320, 4));

@@ -4,6 +4,8 @@
 #include <cstddef>
 #include <cuda_runtime.h>
 
+#include "../../include/rslb.h"
+
 namespace rslb {
 
 enum { kBcFixedEq = 0, kBcOutflow = 1, kBcPeriodic = 2 };
@@ -75,6 +77,12 @@ struct SodLaunch {
 // Opt the stage kernels into large dynamic shared memory (call at set-up,
 // outside stream capture).
 cudaError_t sod_set_attributes();
+// Packed FP32x2 stage kernel (sod32.cu): tile width and threads per CTA
+// (8 threads per cell in the f^eq coefficient phase, a warp per 4 cells in
+// the moments).
+constexpr int kSod32Cells = RSLB_PACKED_TILE_CELLS;
+constexpr int kSod32Threads = 8 * kSod32Cells;
+
 cudaError_t sod32_set_attributes();
 
 // Pick the tile width for V velocities; returns B = 0 if V does not fit.

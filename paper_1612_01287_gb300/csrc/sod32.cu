@@ -1,19 +1,20 @@
 // sod32.cu -- FP32 RK-stage kernel of the Sod shock tube using the packed
 // FP32x2 instructions of sm_100+ (FFMA2 / FADD2 / FMUL2).
 //
-// A CTA owns 28 output cells, split into two halves of 14; one thread walks a
-// velocity row and advances both halves in lock-step, the left half in the x
-// lane and the right half in the y lane of float2 values, so every arithmetic
-// instruction of the sweep does two cells.  Shared memory holds the 36 cells
-// s0-4 .. s0+31 of every velocity row densely (row pitch 144 B, so 16-byte
+// A CTA owns kB2 = RSLB_PACKED_TILE_CELLS output cells, split into two halves
+// of kH; one thread walks a velocity row and advances both halves in
+// lock-step, the left half in the x lane and the right half in the y lane of
+// float2 values, so every arithmetic instruction of the sweep does two cells.
+// Shared memory holds the kB2 + 8 cells s0-4 .. s0+kB2+3 of every velocity
+// row densely (the row pitch is an odd number of 16-byte units, so 16-byte
 // accesses of 8 consecutive rows hit distinct banks); "slot" s of the sweep
-// is the pair (position s, position s+14).  Interior tiles are brought in by
-// tensor-memory-access bulk copies (cp.async.bulk.tensor, one box per block
-// of rows, completion on an mbarrier), boundary tiles by plain loads.  The
-// rest of the stage -- moments (Kahan-compensated FP32 with an error-free
-// FP32 warp reduction), FP64 Landau matching, the f^eq coefficients, WENO5 in
-// difference form, relaxation, RK update -- follows the scalar kernel of
-// sod.cu.
+// is the pair (position s, position s + kH).  Interior tiles are brought in
+// by tensor-memory-access bulk copies (cp.async.bulk.tensor, one box per
+// block of rows, completion on an mbarrier), boundary tiles by plain loads.
+// The rest of the stage -- moments (Kahan-compensated FP32 with an
+// error-free FP32 warp reduction), FP64 Landau matching, the f^eq
+// coefficients, WENO5 in difference form, relaxation, RK update -- follows
+// the scalar kernel of sod.cu.
 #include <cuda.h>
 
 #include <cstring>
@@ -25,11 +26,14 @@
 namespace rslb {
 namespace {
 
-constexpr int kH = 14;          // cells per half
-constexpr int kB2 = 2 * kH;     // output cells per CTA
-constexpr int kC = kB2 + 8;     // cells staged per row: 36
-constexpr int kP = kC;          // floats per row: 36 (144 B)
-constexpr int kNT = 224;        // 7 warps: one per two-slot chunk in the moments
+constexpr int kB2 = kSod32Cells;  // output cells per CTA
+constexpr int kH = kB2 / 2;        // cells per half
+constexpr int kC = kB2 + 8;        // cells staged per row (4-cell halo per side)
+constexpr int kP = kC;             // floats per row (an odd number of 16-byte units)
+constexpr int kNT = kSod32Threads; // a warp per 4 cells in the moments, 8 threads per cell
+                                   // in the f^eq coefficients
+constexpr int kMinCtas = kB2 <= 20 ? 3 : 2;  // CTAs per SM the registers are sized for
+static_assert(kB2 % 4 == 0 && kH % 2 == 0 && (kC / 4) % 2 == 1, "packed tile shape");
 constexpr int kMP = 8;          // coefficient pitch (m) for N_Omega <= 7
 constexpr int kInflight = 8;    // 16-byte global loads in flight per thread (staging, store)
 
@@ -84,7 +88,7 @@ __device__ __forceinline__ void ld2slots(const float* p, float2* out) {
 }
 
 // Slots s, s+1 (s even) of a dense row: x from positions s, s+1, y from
-// positions s+14, s+15.
+// positions s+kH, s+kH+1.
 __device__ __forceinline__ void ld_slot_pair(const float* row, int s, float2* out) {
   const float2 a = *reinterpret_cast<const float2*>(row + s);
   const float2 b = *reinterpret_cast<const float2*>(row + s + kH);
@@ -92,28 +96,17 @@ __device__ __forceinline__ void ld_slot_pair(const float* row, int s, float2* ou
   out[1] = make_float2(a.y, b.y);
 }
 
-template <bool POS>
-__device__ __forceinline__ float2 face_corr2(const float2* J, int wc) {
-  const float2 k13 = splat(13.f / 12.f);
-  auto D = [&](int c) { return sub2(J[c + 1], J[c]); };
-  auto K = [&](int c) {
-    const float2 s2 = sub2(sub2(J[c + 1], J[c]), sub2(J[c], J[c - 1]));
-    return mul2(mul2(k13, s2), s2);
-  };
-  if constexpr (POS)
-    return weno_corr2(D(wc - 2), D(wc - 1), D(wc), D(wc + 1), K(wc - 1), K(wc), K(wc + 1));
-  else
-    return weno_corr2(sub2(splat(0.f), D(wc + 2)), sub2(splat(0.f), D(wc + 1)),
-                      sub2(splat(0.f), D(wc)), sub2(splat(0.f), D(wc - 1)), K(wc + 2),
-                      K(wc + 1), K(wc));
-}
-
-// Sweep a whole row (both halves): slots 4..17 are the outputs; window of
-// 10 slots [i-4, i+6) around the current two-slot chunk i.  Results go back
-// into the row in place: the left-half outputs (positions 4..17) and the
-// right-half outputs of slots >= 8 (positions >= 22) are never read again by
-// the sweep; the right-half outputs of slots 4..7 (positions 18..21) are held
-// until the left half has read those positions (slots 18..21).
+// Sweep a whole row (both halves): slots 4 .. kH+3 are the outputs; window of
+// 10 slots [i-4, i+6) around the current two-slot chunk i, with the first
+// differences D[c] = J[c+1] - J[c] and the smoothness terms
+// K[c] = 13/12 (D[c] - D[c-1])^2 slid along with it (two new of each per
+// chunk).  For xi < 0 the stencil is mirrored; weno_corr2 is odd in its D
+// arguments, so the mirrored correction is taken as -weno_corr2 of the
+// un-negated differences.  Results go back into the row in place: the
+// left-half outputs (positions 4 .. kH+3) and the right-half outputs of slots
+// >= 8 (positions >= kH+8) are never read again by the sweep; the right-half
+// outputs of slots 4..7 (positions kH+4 .. kH+7) are held until the left half
+// has read those positions (its last four slots).
 template <bool POS>
 __device__ __forceinline__ void sweep_row2(float* row, float xi, const float2* wp2, int nm,
                                            const float* __restrict__ ck,
@@ -122,13 +115,30 @@ __device__ __forceinline__ void sweep_row2(float* row, float xi, const float2* w
   constexpr int NW = 10;
   const float2 xi2 = splat(xi);
   const float2 sixth = splat(1.f / 6.f);
-  float2 R[NW], J[NW];
+  const float2 k13 = splat(13.f / 12.f);
+  float2 R[NW], J[NW], Dw[NW - 1], Kw[NW - 1];
   float2 held[2];
 #pragma unroll
   for (int c = 0; c < NW; c += 2) ld_slot_pair(row, c, R + c);
 #pragma unroll
   for (int c = 0; c < NW; ++c) J[c] = mul2(xi2, R[c]);
-  float2 Cl = face_corr2<POS>(J, 3);
+#pragma unroll
+  for (int c = 0; c < NW - 1; ++c) Dw[c] = sub2(J[c + 1], J[c]);
+  Kw[0] = splat(0.f);
+#pragma unroll
+  for (int c = 1; c < NW - 1; ++c) {
+    const float2 d2 = sub2(Dw[c], Dw[c - 1]);
+    Kw[c] = mul2(mul2(k13, d2), d2);
+  }
+  auto face = [&](int wc) {
+    if constexpr (POS)
+      return weno_corr2(Dw[wc - 2], Dw[wc - 1], Dw[wc], Dw[wc + 1], Kw[wc - 1], Kw[wc],
+                        Kw[wc + 1]);
+    else
+      return weno_corr2(Dw[wc + 2], Dw[wc + 1], Dw[wc], Dw[wc - 1], Kw[wc + 2], Kw[wc + 1],
+                        Kw[wc]);
+  };
+  float2 Cl = face(3);
 #pragma unroll
   for (int t = 0; t < kH / 2; ++t) {
     const int i = 4 + 2 * t;  // slot of the first cell of this chunk
@@ -136,9 +146,9 @@ __device__ __forceinline__ void sweep_row2(float* row, float xi, const float2* w
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const int wc = 4 + c;
-      const float2 Cr = face_corr2<POS>(J, wc);
-      const float2 dJ = POS ? sub2(J[wc], J[wc - 1]) : sub2(J[wc + 1], J[wc]);
-      const float2 dF = fma2(sub2(Cr, Cl), sixth, dJ);
+      const float2 Cr = face(wc);
+      const float2 dF = POS ? fma2(sub2(Cr, Cl), sixth, Dw[wc - 1])
+                            : fma2(sub2(Cl, Cr), sixth, Dw[wc]);
       Cl = Cr;
       // f^eq for the two cells of this slot: coefficients (x cell, y cell) per m
       const float* cc = ck + (size_t)(i + c - 4) * (2 * kMP);
@@ -166,9 +176,20 @@ __device__ __forceinline__ void sweep_row2(float* row, float xi, const float2* w
         J[c] = J[c + 2];
         R[c] = R[c + 2];
       }
+#pragma unroll
+      for (int c = 0; c < NW - 3; ++c) {
+        Dw[c] = Dw[c + 2];
+        Kw[c] = Kw[c + 2];
+      }
       ld_slot_pair(row, i + 6, R + NW - 2);  // slots i+6, i+7
       J[NW - 2] = mul2(xi2, R[NW - 2]);
       J[NW - 1] = mul2(xi2, R[NW - 1]);
+#pragma unroll
+      for (int c = NW - 3; c < NW - 1; ++c) {
+        Dw[c] = sub2(J[c + 1], J[c]);
+        const float2 d2 = sub2(Dw[c], Dw[c - 1]);
+        Kw[c] = mul2(mul2(k13, d2), d2);
+      }
     }
     *reinterpret_cast<float2*>(row + i) = make_float2(out[0].x, out[1].x);
     if (t < 2) {
@@ -176,7 +197,7 @@ __device__ __forceinline__ void sweep_row2(float* row, float xi, const float2* w
     } else {
       *reinterpret_cast<float2*>(row + i + kH) = make_float2(out[0].y, out[1].y);
     }
-    if (t == 5) {  // slots 20, 21 have just been read
+    if (t == kH / 2 - 2) {  // the last two slots have just been read
       *reinterpret_cast<float2*>(row + 4 + kH) = held[0];
       *reinterpret_cast<float2*>(row + 6 + kH) = held[1];
     }
@@ -203,7 +224,7 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 static int tma_box_rows(int V, int* nbox) {
   const int nb = (V + 255) / 256;
   int r = (V + nb - 1) / nb;
-  r = (r + 7) / 8 * 8;  // a box is 144 r bytes: a multiple of 128 B
+  r = (r + 7) / 8 * 8;  // a box is 4 kC r bytes: a multiple of 128 B
   if (nbox) *nbox = nb;
   return r;
 }
@@ -245,7 +266,7 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // ---- 1. stage rows: cell s0-4+p goes to position p (0 <= p < 36) ----
+  // ---- 1. stage rows: cell s0-4+p goes to position p (0 <= p < kC) ----
   const bool interior = (s0 - 4 >= 0) && (s0 + kB2 + 4 <= g.Z);
   if (interior && tmap) {
     // one thread issues the box copies; everyone waits on the mbarrier
@@ -279,21 +300,21 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
   } else if (interior) {
     // eight 16-byte loads in flight per thread before the shared-memory stores
     const float* src = fin + s0 - 4;
-    for (int base_i = tid; base_i < V * 9; base_i += kInflight * kNT) {
+    for (int base_i = tid; base_i < V * (kC / 4); base_i += kInflight * kNT) {
       float4 x[kInflight];
 #pragma unroll
       for (int u = 0; u < kInflight; ++u) {
         const int idx = base_i + u * kNT;
-        if (idx < V * 9) {
-          const int v = idx / 9, q = idx - v * 9;
+        if (idx < V * (kC / 4)) {
+          const int v = idx / (kC / 4), q = idx - v * (kC / 4);
           x[u] = __ldg(reinterpret_cast<const float4*>(src + (size_t)v * g.ldz + 4 * q));
         }
       }
 #pragma unroll
       for (int u = 0; u < kInflight; ++u) {
         const int idx = base_i + u * kNT;
-        if (idx < V * 9) {
-          const int v = idx / 9, q = idx - v * 9;
+        if (idx < V * (kC / 4)) {
+          const int v = idx / (kC / 4), q = idx - v * (kC / 4);
           *reinterpret_cast<float4*>(tile + v * kP + 4 * q) = x[u];
         }
       }
@@ -423,7 +444,7 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
 
     // ---- 3b. f^eq coefficients: 8 threads per cell share the 32 nodes ----
     {
-      const int c = tid >> 3, q = tid & 7;  // 28 cells x 8 = 224 threads
+      const int c = tid >> 3, q = tid & 7;  // 8 threads per cell
       const float ud = cellf[2 * kB2 + c];
       const float A = cellf[3 * kB2 + c], sh2 = cellf[5 * kB2 + c];
       const float uinv = (ud > 0.f) ? 1.f / ud : 0.f;
@@ -488,23 +509,23 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
   const float a = (stage == 1) ? 0.75f : 1.f / 3.f;
   const float b = (stage == 1) ? 0.25f : 2.f / 3.f;
   if (s0 + kB2 <= g.Z) {
-    // full tile: 7 chunks of 4 cells per row, 16-byte accesses, eight loads
+    // full tile: kB2/4 chunks of 4 cells per row, 16-byte accesses, eight loads
     // of f_n in flight per thread
-    for (int base_i = tid; base_i < V * 7; base_i += kInflight * kNT) {
+    for (int base_i = tid; base_i < V * (kB2 / 4); base_i += kInflight * kNT) {
       float4 fo[kInflight];
 #pragma unroll
       for (int u = 0; u < kInflight; ++u) {
         const int idx = base_i + u * kNT;
-        if (stage != 0 && idx < V * 7) {
-          const int v = idx / 7, q = idx - v * 7;
+        if (stage != 0 && idx < V * (kB2 / 4)) {
+          const int v = idx / (kB2 / 4), q = idx - v * (kB2 / 4);
           fo[u] = __ldg(reinterpret_cast<const float4*>(fn + (size_t)v * g.ldz + s0 + 4 * q));
         }
       }
 #pragma unroll
       for (int u = 0; u < kInflight; ++u) {
         const int idx = base_i + u * kNT;
-        if (idx < V * 7) {
-          const int v = idx / 7, q = idx - v * 7;
+        if (idx < V * (kB2 / 4)) {
+          const int v = idx / (kB2 / 4), q = idx - v * (kB2 / 4);
           float4 r = *reinterpret_cast<const float4*>(tile + v * kP + 4 + 4 * q);
           if (stage != 0) {
             r.x = a * fo[u].x + b * r.x;
@@ -530,7 +551,7 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
   }
 }
 
-__global__ void __launch_bounds__(kNT, 2)
+__global__ void __launch_bounds__(kNT, kMinCtas)
 sod32_stage_kernel(const float* __restrict__ fin, const float* __restrict__ fn, float* fout,
                    int stage, int* err, SodGeom g, SodTables<float> tb, const int* __restrict__ rowv,
                    int nneg, const __grid_constant__ CUtensorMap tmap, int use_tma, int box_rows,
@@ -541,7 +562,7 @@ sod32_stage_kernel(const float* __restrict__ fin, const float* __restrict__ fn, 
 
 // Batched: a persistent grid walks the task list of all runs of one class
 // (plain-load staging).
-__global__ void __launch_bounds__(kNT, 2)
+__global__ void __launch_bounds__(kNT, kMinCtas)
 sod32_batch_kernel(const SodRunDesc<float>* __restrict__ runs, const SodTask* __restrict__ tasks,
                    int ntasks, const long long* __restrict__ step, int stage, int* err) {
   const long long n = *step;
@@ -584,7 +605,7 @@ EncodeTiled encode_fn() {
 }
 
 // Tensor map of one population buffer: 2-D FP32 [V][Z] with row stride ldz,
-// box 36 cells x box_rows rows, zero fill outside.
+// box kC cells x box_rows rows, zero fill outside.
 bool make_map(CUtensorMap* m, const float* f, int Z, int ldz, int V, int box_rows) {
   EncodeTiled enc = encode_fn();
   if (!enc) return false;

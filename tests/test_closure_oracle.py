@@ -113,12 +113,29 @@ def test_features_layout():
     f = np.arange(12.0).reshape(4, 3) + 1.0
     X = C.features(f, 0.1)
     n = f.sum(1)
-    assert np.allclose(X[0, :3], f[0] / n[0])      # outflow copy at the left end
-    assert np.allclose(X[1, :3], f[0] / n[1])
-    assert np.allclose(X[1, 3:6], f[1] / n[1])
-    assert np.allclose(X[1, 6:9], f[2] / n[1])
-    assert np.allclose(X[3, 6:9], f[3] / n[3])      # outflow copy at the right end
+    assert np.allclose(X[1, :3], f[1] / n[1])
+    assert np.allclose(X[1, 3:6], (f[2] - f[1]) / n[1])
+    assert np.allclose(X[1, 6:9], (f[1] - f[0]) / n[1])
+    assert np.allclose(X[0, 6:9], 0.0)      # outflow copy at the left end
+    assert np.allclose(X[3, 3:6], 0.0)      # outflow copy at the right end
     assert np.allclose(X[:, 9], -1.0)
+
+
+def test_normalization_fit_and_use():
+    rng = np.random.default_rng(8)
+    X = rng.normal(3.0, 2.0, size=(5000, 4))
+    X[:, 2] = 7.0  # constant column
+    T = rng.normal(0.0, 0.5, size=(5000, 2))
+    mu, isd, osd = C.fit_normalization(X, T)
+    Xn = (X - mu) * isd
+    assert np.abs(Xn[:, [0, 1, 3]].mean(0)).max() < 1e-12
+    assert np.abs(Xn[:, [0, 1, 3]].std(0) - 1).max() < 1e-12
+    assert isd[2] == 1.0 and np.all(Xn[:, 2] == 0.0)
+    assert np.allclose(np.sqrt((T / osd) ** 2).mean(0) > 0, True)
+    assert np.abs(np.sqrt(((T / osd) ** 2).mean(0)) - 1).max() < 1e-12
+    theta = rng.normal(0, 0.3, size=sum(C.param_sizes(4, 16, 2)))
+    y0, _ = C.forward(theta, Xn, 4, 16, 2)
+    assert np.allclose(C.net(theta, X, 4, 16, 2, (mu, isd, osd)), y0 * osd, rtol=1e-14)
 
 
 def test_bf16_rounding():

@@ -60,20 +60,53 @@ def test_restriction_matches_oracle():
     assert np.abs(fl - ref).max() <= 2e-6 * np.abs(ref).max()
 
 
+def random_norm(rng):
+    mu = rng.normal(0, 0.5, size=D).astype(np.float32)
+    isd = rng.uniform(0.5, 3.0, size=D).astype(np.float32)
+    osd = rng.uniform(1e-3, 1e-1, size=O).astype(np.float32)
+    return mu, isd, osd
+
+
+def f64(norm):
+    return tuple(np.asarray(a, dtype=np.float64) for a in norm)
+
+
 def test_mlp_forward_matches_oracle():
     import torch
     from paper_1612_01287_gb300 import MLP
     rng = np.random.default_rng(1)
     X = rng.normal(0, 1, size=(300, D)).astype(np.float32)
+    norm = random_norm(rng)
     with MLP(D, H, O, seed=7) as m:
+        m.set_normalization(*norm)
+        back = m.get_normalization()
+        assert all(np.array_equal(a, b) for a, b in zip(back, norm))
         Xd = torch.from_numpy(X).cuda()
         Yd = torch.zeros((300, O), dtype=torch.float32, device="cuda")
         m.forward(Xd.data_ptr(), 300, Yd.data_ptr())
         torch.cuda.synchronize()
         th = oracle_theta(m.get_params())
-    ref, _ = C.forward(th, X.astype(np.float64), D, H, O)
+    ref = C.net(th, X.astype(np.float64), D, H, O, f64(norm))
     got = Yd.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_fit_normalization_matches_column_statistics():
+    import torch
+    from paper_1612_01287_gb300 import MLP
+    rng = np.random.default_rng(6)
+    X = rng.normal(2.0, 0.3, size=(20000, D)).astype(np.float32)
+    X[:, -1] = -1.0  # a constant column (log10 tau of a single run)
+    T = rng.normal(0, 1e-4, size=(20000, O)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()  # kept alive
+    with MLP(D, H, O, seed=1) as m:
+        m.fit_normalization(Xd.data_ptr(), Td.data_ptr(), 20000)
+        mu, isd, osd = m.get_normalization()
+    rmu, risd, rosd = C.fit_normalization(X, T)
+    assert np.abs(mu - rmu).max() <= 1e-6 * np.abs(rmu).max()
+    assert np.abs(isd - risd).max() <= 1e-5 * np.abs(risd).max()
+    assert np.abs(osd - rosd).max() <= 1e-5 * np.abs(rosd).max()
+    assert isd[-1] == 1.0
 
 
 def test_mlp_gradient_matches_oracle():
@@ -85,21 +118,26 @@ def test_mlp_gradient_matches_oracle():
     N = 256
     X = rng.normal(0, 1, size=(N, D)).astype(np.float32)
     T = rng.normal(0, 0.1, size=(N, O)).astype(np.float32)
+    norm = random_norm(rng)
     with MLP(D, H, O, seed=3) as m:
         theta = m.get_params()
         theta[-O:] = rng.normal(0, 0.1, size=O)  # non-zero output biases
         theta[D * H:D * H + H] = rng.normal(0, 0.1, size=H)
         m.set_params(theta)
+        m.set_normalization(*norm)
         Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
         loss, g = m.loss_grad(Xd.data_ptr(), Td.data_ptr(), N)
         th = oracle_theta(m.get_params())
-    Lr, gr = C.loss_grad(th, X.astype(np.float64), T.astype(np.float64), D, H, O)
+    mu, isd, osd = f64(norm)
+    Xn = (X.astype(np.float64) - mu) * isd
+    Tn = T.astype(np.float64) / osd
+    Lr, gr = C.loss_grad(th, Xn, Tn, D, H, O)
     assert abs(loss - Lr) <= 1e-5 * Lr
     rel = np.abs(g - gr).max() / np.abs(gr).max()
     print("gradient vs FP64 backprop:", rel)
     assert rel <= 1e-3
     idx = rng.choice(len(th), size=1000, replace=False)
-    fd = C.fd_grad(th, X.astype(np.float64), T.astype(np.float64), D, H, O, idx, h=1e-4)
+    fd = C.fd_grad(th, Xn, Tn, D, H, O, idx, h=1e-4)
     rel_fd = np.abs(g[idx] - fd).max() / np.abs(fd).max()
     print("gradient vs oracle finite differences:", rel_fd)
     assert rel_fd <= 1e-3
@@ -135,17 +173,20 @@ def test_closure_step_matches_oracle_and_conserves():
     n, T0, b = workloads.random_smooth_fields(Z, beta_max=0.4)
     kw = dict(Z=Z, Q_xi=QLO, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", tau=tau, dt=dt,
               fields=(n, T0, b))
+    rng = np.random.default_rng(12)
+    norm = random_norm(rng)
     with MLP(D, H, O, seed=5) as m, Sod(**kw) as a, Sod(**kw) as c:
         th = m.get_params()
         th[D * H + H + H * H + H:] *= 10.0  # a visible correction
         m.set_params(th)
+        m.set_normalization(*norm)
         a.step(1)
         closure_step(c, m, tau, 1)
         fa = a.get_state().astype(np.float64).T
         fc = c.get_state().astype(np.float64).T
         thr = oracle_theta(m.get_params())
     d = fc - fa
-    ref = C.correction(thr, fa, tau, QLO, QL, H)
+    ref = C.correction(thr, fa, tau, QLO, QL, H, f64(norm))
     assert np.abs(ref).max() > 1e-4 * np.abs(fa).max()
     assert np.abs(d - ref).max() <= 1e-5 * np.abs(fa).max()
     Phi, _ = C.invariants(QLO, QL)
@@ -183,6 +224,7 @@ def test_trained_closure_lowers_low_order_error():
 
     res = {}
     with MLP(D, H, O, seed=11) as m:
+        m.fit_normalization(X.data_ptr(), T.data_ptr(), N)
         losses = m.train(X.data_ptr(), T.data_ptr(), N, epochs=30, batch=2048, lr=2e-3, seed=1)
         print("training samples", N, "loss first/last epoch", losses[0], losses[-1])
         assert losses[-1] < 0.5 * losses[0]

@@ -13,6 +13,8 @@ import oracle
 from paper_1612_01287_gb300 import workloads
 from tests import sodcase
 
+from paper_1612_01287_gb300._lib import PACKED_TILE_CELLS as PACKED  # noqa: E402
+
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
@@ -115,7 +117,7 @@ def test_large_velocity_sets(precision, tol, Q_xi):
     sodcase.compare(case, 6, precision, tol, tol if precision == "f64" else None)
 
 
-@pytest.mark.parametrize("precision,tiles,tol", [("f32", (28, 32, 16), 1e-6),
+@pytest.mark.parametrize("precision,tiles,tol", [("f32", (PACKED, 32, 16), 1e-6),
                                                  ("f64", (16, 8), 1e-13)])
 def test_tile_width_does_not_change_results(precision, tiles, tol):
     from paper_1612_01287_gb300 import Sod
