@@ -145,11 +145,22 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def source_sha():
+KERNEL_SOURCES = {
+    # the sources a stage kernel is compiled from
+    "sod32_stage_kernel": ("paper_1612_01287_gb300/csrc/sod32.cu",
+                           "paper_1612_01287_gb300/csrc/sod.cuh",
+                           "paper_1612_01287_gb300/csrc/rslb_device.cuh", "include/rslb.h"),
+}
+
+
+def source_sha(kernel="sod32_stage_kernel"):
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1612_01287_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    files = KERNEL_SOURCES.get(kernel)
+    if files is None:
+        csrc = os.path.join(ROOT, "paper_1612_01287_gb300", "csrc")
+        files = [os.path.join("paper_1612_01287_gb300", "csrc", f) for f in sorted(os.listdir(csrc))]
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -160,7 +171,7 @@ def recorded_traffic(kernel):
         return None
     try:
         d = json.load(open(path)).get(kernel)
-        if d and d.get("source_sha") == source_sha():
+        if d and d.get("source_sha") == source_sha(kernel):
             return d.get("dram_bytes_per_launch")
     except Exception:
         pass

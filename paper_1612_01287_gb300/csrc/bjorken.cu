@@ -588,7 +588,9 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
     rc = set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cudaMalloc failed");
   if (!rc && cudaMalloc(&b->state, es * (size_t)b->total_state) != cudaSuccess)
     rc = set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cannot allocate the state");
-  if (!rc && cudaMalloc(&b->kpool, es * (size_t)kp_total) != cudaSuccess)
+  // the SIMT K^P pool (the tensor-core path uses its own image instead)
+  if (!rc && o->kp_mode != RSLB_KP_TF32X3 &&
+      cudaMalloc(&b->kpool, es * (size_t)kp_total) != cudaSuccess)
     rc = set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cannot allocate K^P (%lld entries)",
                    kp_total);
   if (!rc && cudaMalloc((void**)&b->err, 2 * sizeof(int)) != cudaSuccess)
@@ -612,7 +614,7 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
   cudaStream_t st = b->stream;
   cudaMemsetAsync(b->err, 0, 2 * sizeof(int), st);
   // K^P per distinct Q, K^L, initial state
-  for (size_t i = 0; i < qvals.size(); ++i) {
+  for (size_t i = 0; i < qvals.size() && o->kp_mode != RSLB_KP_TF32X3; ++i) {
     const int Q = qvals[i];
     const int n = Q * Q;
     if (b->precision == RSLB_F64)

@@ -34,7 +34,8 @@
 namespace rslb {
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 160;  // 4 worker warps + 1 issuer warp
+constexpr int kTcWorkers = 128;
 constexpr uint32_t kATile = 128 * 128;  // bytes: 128 rows x 32 FP32
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kErrTimeout = 97;
@@ -46,6 +47,10 @@ __device__ __forceinline__ uint32_t su32(const void* p) {
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -190,8 +195,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
   auto Bhi = [&](int s) { return base + s * sstride + 2 * kATile; };
   auto Blo = [&](int s) { return base + s * sstride + 2 * kATile + btile; };
   unsigned char* tail = base + 2 * sstride;
-  uint64_t* full = reinterpret_cast<uint64_t*>(tail);  // [2]
-  uint64_t* done = full + 2;                           // [2]
+  uint64_t* full = reinterpret_cast<uint64_t*>(tail);  // [2] K^P tile landed
+  uint64_t* ready = full + 2;                          // [2] workers filled the stage
+  uint64_t* done = ready + 2;                          // [2] MMAs of the stage finished
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 2);
   float* rs = reinterpret_cast<float*>(tail + 64);  // rate[R] | neq4[R] | omt[R]
   float* mp = rs + 3 * R;                           // [4 warps][R][2]
@@ -207,6 +213,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
   if (tid == 0) {
     mbar_init(&full[0], 1);
     mbar_init(&full[1], 1);
+    mbar_init(&ready[0], kTcWorkers);
+    mbar_init(&ready[1], kTcWorkers);
     mbar_init(&done[0], 1);
     mbar_init(&done[1], 1);
     fence_mbar_init();
@@ -227,12 +235,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
   const float* Asrc = a.kimg + blk.img + (size_t)mt * 128 * nkb * 32;
   const uint32_t abytes = (uint32_t)rows * 128u;
   const uint32_t idesc = idesc_tf32(NC);
-  // issued-but-unconfirmed work of thread 0 (for the abort path)
+  // The issuer (lane 0 of warp 4) keeps the bulk copies two K-blocks ahead
+  // and issues the MMAs; issued-but-unconfirmed work is tracked for the
+  // abort path.
+  const bool issuer = tid == kTcWorkers;
   int last_copy = -1, last_commit = -1;
-  if (tid == 0) {
-    mbar_expect_tx(&full[0], abytes);
-    bulk_g2s(Ahi(0), Asrc, abytes, &full[0]);
-    last_copy = 0;
+  if (issuer) {
+    for (int it = 0; it < 2 && it < nkb; ++it) {
+      mbar_expect_tx(&full[it], abytes);
+      bulk_g2s(Ahi(it), Asrc + (size_t)it * rows * 32, abytes, &full[it]);
+      last_copy = it;
+    }
   }
 
   // per-run equilibrium of the stage state from the moment partials
@@ -273,58 +286,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
   }
 
   // ---- main loop over K-blocks of 32 rows j' ----
-  // The state rows of K-block it+1 are loaded into registers while K-block it
-  // is split and multiplied; every thread checks for itself that the MMAs
-  // that last read a B buffer are done before overwriting it, so one CTA
-  // barrier per K-block suffices.
+  // Workers (warps 0-3): store the state rows of K-block it (loaded into
+  // registers during it-1) split into hi/lo, load those of it+1, split the
+  // landed K^P tile in place and arrive on ready[s].  Issuer: wait ready[s],
+  // issue the 12 MMAs, commit to done[s]; once they are done, refill stage s
+  // with the K^P tile of it+2.  No CTA-wide barrier inside the loop.
   const float* Fblk = a.Fin + blk.soff;
-  float bv[kTcMaxRowsPerWarp];
-  auto load_b = [&](int it) {
-    const int jj = it * 32 + lane;
-#pragma unroll
-    for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
-      const int c = warp + 4 * u;
-      bv[u] = (c < ncv && jj < Q) ? Fblk[(size_t)c * Q + jj] : 0.f;
-    }
-  };
-  load_b(0);
-  bool aborted = false;
   int lost = 0;
-  for (int it = 0; it < nkb; ++it) {
-    const int s = it & 1;
-    const uint32_t par = (uint32_t)(it >> 1) & 1u;
-    // B buffer s was last read by the MMAs of it-2
-    if (it >= 2 && !mbar_wait(&done[s], (uint32_t)((it - 2) >> 1) & 1u)) lost = 1;
-#pragma unroll
-    for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
-      const int c = warp + 4 * u;
-      if (c < NC) {
-        const float hi = tf32_rn(bv[u]);
-        const uint32_t o = swz(c, lane);
-        *reinterpret_cast<float*>(Bhi(s) + o) = hi;
-        *reinterpret_cast<float*>(Blo(s) + o) = bv[u] - hi;
+  if (issuer) {
+    for (int it = 0; it < nkb; ++it) {
+      const int s = it & 1;
+      const uint32_t par = (uint32_t)(it >> 1) & 1u;
+      if (!mbar_wait(&ready[s], par)) {
+        lost = 1;
+        break;
       }
-    }
-    if (it + 1 < nkb) load_b(it + 1);
-    // K^P tile of this K-block: wait for the bulk copy, split in place
-    if (!mbar_wait(&full[s], par)) lost = 1;
-    {
-      float4* ah = reinterpret_cast<float4*>(Ahi(s));
-      float4* al = reinterpret_cast<float4*>(Alo(s));
-      for (int i = tid; i < rows * 8; i += kTcThreads) {
-        const float4 x = ah[i];
-        const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
-        ah[i] = h;
-        al[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-      }
-    }
-    fence_proxy_async();
-    if (__syncthreads_or(lost)) {
-      if (tid == 0) tc_report(a.err, kErrTimeout, blk.first);
-      aborted = true;
-      break;
-    }
-    if (tid == 0) {
       tc_fence_after();
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
@@ -336,29 +312,75 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
       }
       mma_commit(&done[s]);
       last_commit = it;
-      if (it + 1 < nkb) {
-        // A buffer (it+1)&1 was last read by the MMAs of it-1
-        if (it == 0 || mbar_wait(&done[(it - 1) & 1], (uint32_t)((it - 1) >> 1) & 1u)) {
-          mbar_expect_tx(&full[(it + 1) & 1], abytes);
-          bulk_g2s(Ahi((it + 1) & 1), Asrc + (size_t)(it + 1) * rows * 32, abytes,
-                   &full[(it + 1) & 1]);
-          last_copy = it + 1;
-        } else {
-          lost = 1;  // reported at the next barrier
+      if (it + 2 < nkb) {
+        if (!mbar_wait(&done[s], par)) {
+          lost = 1;
+          break;
         }
+        mbar_expect_tx(&full[s], abytes);
+        bulk_g2s(Ahi(s), Asrc + (size_t)(it + 2) * rows * 32, abytes, &full[s]);
+        last_copy = it + 2;
       }
     }
+  } else if (warp < 4) {
+    float bv[kTcMaxRowsPerWarp];
+    auto load_b = [&](int it) {
+      const int jj = it * 32 + lane;
+#pragma unroll
+      for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
+        const int c = warp + 4 * u;
+        bv[u] = (c < ncv && jj < Q) ? Fblk[(size_t)c * Q + jj] : 0.f;
+      }
+    };
+    load_b(0);
+    for (int it = 0; it < nkb; ++it) {
+      const int s = it & 1;
+      const uint32_t par = (uint32_t)(it >> 1) & 1u;
+      // stage s was last read by the MMAs of it-2
+      if (it >= 2 && !mbar_wait(&done[s], (uint32_t)((it - 2) >> 1) & 1u)) {
+        lost = 1;
+        break;
+      }
+#pragma unroll
+      for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
+        const int c = warp + 4 * u;
+        if (c < NC) {
+          const float hi = tf32_rn(bv[u]);
+          const uint32_t o = swz(c, lane);
+          *reinterpret_cast<float*>(Bhi(s) + o) = hi;
+          *reinterpret_cast<float*>(Blo(s) + o) = bv[u] - hi;
+        }
+      }
+      if (it + 1 < nkb) load_b(it + 1);
+      if (!mbar_wait(&full[s], par)) {
+        lost = 1;
+        break;
+      }
+      float4* ah = reinterpret_cast<float4*>(Ahi(s));
+      float4* al = reinterpret_cast<float4*>(Alo(s));
+      for (int i = tid; i < rows * 8; i += kTcWorkers) {
+        const float4 x = ah[i];
+        const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
+        ah[i] = h;
+        al[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+      fence_proxy_async();
+      mbar_arrive(&ready[s]);
+    }
+    // the last commit completes after all earlier MMAs
+    if (!lost && !mbar_wait(&done[(nkb - 1) & 1], (uint32_t)((nkb - 1) >> 1) & 1u)) lost = 1;
   }
-
   // all MMAs done (commits complete in issue order); the outcome is made
   // uniform across the CTA before anyone branches on it
-  lost = aborted ? 1 : !mbar_wait(&done[(nkb - 1) & 1], (uint32_t)((nkb - 1) >> 1) & 1u);
   if (__syncthreads_or(lost)) {
-    if (tid == 0 && !aborted) tc_report(a.err, kErrTimeout, blk.first);
-    // bounded wait for what thread 0 issued, then release tensor memory
-    if (tid == 0) {
+    if (tid == 0) tc_report(a.err, kErrTimeout, blk.first);
+    // bounded wait for what the issuer issued, then release tensor memory
+    if (issuer) {
       if (last_commit >= 0) mbar_wait(&done[last_commit & 1], (uint32_t)(last_commit >> 1) & 1u);
-      if (last_copy > last_commit) mbar_wait(&full[last_copy & 1], (uint32_t)(last_copy >> 1) & 1u);
+      // up to two copies may still be in flight
+      for (int c = last_copy > last_commit + 1 ? last_copy - 1 : last_commit + 1; c <= last_copy;
+           ++c)
+        mbar_wait(&full[c & 1], (uint32_t)(c >> 1) & 1u);
     }
     tc_fence_before();
     __syncthreads();
@@ -372,76 +394,78 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
   }
   tc_fence_after();
 
-  // ---- epilogue: row j of D per thread ----
-  const int j = 128 * mt + 32 * warp + lane;
-  const bool rowok = j < Q;
-  float xi2 = 0.f, wj = 0.f;
-  if (rowok) {
-    const double x = a.npool[blk.xoff + j];
-    xi2 = float(x * x);
-    wj = float(a.npool[blk.xoff + Q + j]);
-  }
-  float KL[QL * QL], xk[QL], wk[QL], l1[QL];
+  // ---- epilogue (worker warps): row j of D per thread ----
+  if (warp < 4) {
+    const int j = 128 * mt + 32 * warp + lane;
+    const bool rowok = j < Q;
+    float xi2 = 0.f, wj = 0.f;
+    if (rowok) {
+      const double x = a.npool[blk.xoff + j];
+      xi2 = float(x * x);
+      wj = float(a.npool[blk.xoff + Q + j]);
+    }
+    float KL[QL * QL], xk[QL], wk[QL], l1[QL];
 #pragma unroll
-  for (int k = 0; k < QL; ++k) {
-    xk[k] = float(a.xk[k]);
-    wk[k] = float(a.wk[k]);
-    l1[k] = float(3.0 - a.xk[k]);
+    for (int k = 0; k < QL; ++k) {
+      xk[k] = float(a.xk[k]);
+      wk[k] = float(a.wk[k]);
+      l1[k] = float(3.0 - a.xk[k]);
 #pragma unroll
-    for (int q = 0; q < QL; ++q) KL[k * QL + q] = float(a.KL[k * QL + q]);
-  }
-  const float itau = float(1.0 / a.tau), dt = float(a.dtau);
-  const float ca = a.stage == 1 ? 0.75f : 1.f / 3.f, cb = a.stage == 1 ? 0.25f : 2.f / 3.f;
-  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-  const float* Fin = a.Fin + blk.soff;
-  const float* Fn = a.Fn + blk.soff;
-  float* Fout = a.Fout + blk.soff;
-  for (int rb = 0; rb < R; rb += 16) {
-    const int c0 = rb * QL;
-    uint32_t d[16 * QL];
+      for (int q = 0; q < QL; ++q) KL[k * QL + q] = float(a.KL[k * QL + q]);
+    }
+    const float itau = float(1.0 / a.tau), dt = float(a.dtau);
+    const float ca = a.stage == 1 ? 0.75f : 1.f / 3.f, cb = a.stage == 1 ? 0.25f : 2.f / 3.f;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    const float* Fin = a.Fin + blk.soff;
+    const float* Fn = a.Fn + blk.soff;
+    float* Fout = a.Fout + blk.soff;
+    for (int rb = 0; rb < R; rb += 16) {
+      const int c0 = rb * QL;
+      uint32_t d[16 * QL];
 #pragma unroll
-    for (int p = 0; p < QL; ++p)
-      if (c0 + 16 * p < NC) tmem_ld16(trow + (uint32_t)(c0 + 16 * p), d + 16 * p);
-    tmem_wait_ld();
+      for (int p = 0; p < QL; ++p)
+        if (c0 + 16 * p < NC) tmem_ld16(trow + (uint32_t)(c0 + 16 * p), d + 16 * p);
+      tmem_wait_ld();
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int r = rb + i;
-      float on = 0.f, oe = 0.f;
-      if (r < R && rowok) {
-        float fk[QL];
+      for (int i = 0; i < 16; ++i) {
+        const int r = rb + i;
+        float on = 0.f, oe = 0.f;
+        if (r < R && rowok) {
+          float fk[QL];
 #pragma unroll
-        for (int k = 0; k < QL; ++k) fk[k] = Fin[(size_t)(r * QL + k) * Q + j];
-        if (!rk) {
+          for (int k = 0; k < QL; ++k) fk[k] = Fin[(size_t)(r * QL + k) * Q + j];
+          if (!rk) {
 #pragma unroll
-          for (int k = 0; k < QL; ++k)
-            a.dout[blk.soff + (size_t)(r * QL + k) * Q + j] = __uint_as_float(d[i * QL + k]);
-        } else {
-          const float rate = rs[r], neq4 = rs[R + r], omt = rs[2 * R + r];
+            for (int k = 0; k < QL; ++k)
+              a.dout[blk.soff + (size_t)(r * QL + k) * Q + j] = __uint_as_float(d[i * QL + k]);
+          } else {
+            const float rate = rs[r], neq4 = rs[R + r], omt = rs[2 * R + r];
 #pragma unroll
-          for (int k = 0; k < QL; ++k) {
-            float klf = 0.f;
+            for (int k = 0; k < QL; ++k) {
+              float klf = 0.f;
 #pragma unroll
-            for (int q = 0; q < QL; ++q) klf += KL[k * QL + q] * fk[q];
-            const float feq = neq4 * (wj * wk[k]) * (1.f + l1[k] * omt);
-            const float L = (-fk[k] + xi2 * klf + __uint_as_float(d[i * QL + k])) * itau -
-                            (fk[k] - feq) * rate;
-            const float v = fk[k] + dt * L;
-            const size_t o = (size_t)(r * QL + k) * Q + j;
-            float out = v;
-            if (a.stage == 1) out = ca * Fn[o] + cb * v;
-            else if (a.stage == 2) out = Fn[o] * ca + cb * v;
-            Fout[o] = out;
-            on += out;
-            oe += xk[k] * out;
+              for (int q = 0; q < QL; ++q) klf += KL[k * QL + q] * fk[q];
+              const float feq = neq4 * (wj * wk[k]) * (1.f + l1[k] * omt);
+              const float L = (-fk[k] + xi2 * klf + __uint_as_float(d[i * QL + k])) * itau -
+                              (fk[k] - feq) * rate;
+              const float v = fk[k] + dt * L;
+              const size_t o = (size_t)(r * QL + k) * Q + j;
+              float out = v;
+              if (a.stage == 1) out = ca * Fn[o] + cb * v;
+              else if (a.stage == 2) out = Fn[o] * ca + cb * v;
+              Fout[o] = out;
+              on += out;
+              oe += xk[k] * out;
+            }
           }
         }
-      }
-      if (rk) {
-        on = warp_sum_f(on);
-        oe = warp_sum_f(oe);
-        if (lane == 0 && r < R) {
-          mp[(warp * R + r) * 2] = on;
-          mp[(warp * R + r) * 2 + 1] = oe;
+        if (rk) {
+          on = warp_sum_f(on);
+          oe = warp_sum_f(oe);
+          if (lane == 0 && r < R) {
+            mp[(warp * R + r) * 2] = on;
+            mp[(warp * R + r) * 2 + 1] = oe;
+          }
         }
       }
     }

@@ -220,7 +220,8 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 
 // Shared memory: tile [rows][kP] floats (rows = V rounded up to whole TMA
 // boxes), then partial moments, cell scalars, coefficients
-// [QL][kH][kMP][2] floats, gco [kH][4] floats and an mbarrier.
+// [QL][kH][kMP][2] floats, gco [kH][4] floats, an mbarrier and the five
+// moment weights of every velocity [5][V].
 static int tma_box_rows(int V, int* nbox) {
   const int nb = (V + 255) / 256;
   int r = (V + nb - 1) / nb;
@@ -239,7 +240,7 @@ size_t sod32_smem_bytes(int V, int QL) {
   auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
   return al(sizeof(float) * tile_rows(V) * kP) + al(sizeof(double) * 5 * kB2) +
          al(sizeof(double) * 8 * kB2) + al(sizeof(float) * (size_t)QL * kH * kMP * 2) +
-         al(sizeof(float) * kH * 4) + 128 + 128;
+         al(sizeof(float) * kH * 4) + 128 + al(sizeof(float) * 5 * (size_t)V) + 128;
 }
 
 // One stage of one tile starting at cell s0 (the whole CTA).
@@ -247,8 +248,8 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
                                            const float* __restrict__ fn, float* fout, int stage,
                                            int* err, const SodGeom& g, const SodTables<float>& tb,
                                            const int* __restrict__ rowv, int nneg, int s0,
-                                           const CUtensorMap* tmap, int box_rows, int nbox,
-                                           uint32_t phase) {
+                                           const CUtensorMap* tmap, const CUtensorMap* fnmap,
+                                           int box_rows, int nbox, uint32_t phase) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
   const int V = g.V;
@@ -263,6 +264,10 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
   float* gco = coef + (size_t)g.QL * kH * kMP * 2;  // [kH][g0x g0y g1x g1y]
   uint64_t* bar = reinterpret_cast<uint64_t*>(
       reinterpret_cast<unsigned char*>(gco) + al(sizeof(float) * kH * 4));
+  float* mws = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bar) + 128);
+  auto copy_weights = [&]() {
+    for (int e = threadIdx.x; e < 5 * V; e += kNT) mws[e] = tb.mw[e];
+  };
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -284,8 +289,17 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
             " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(tile + (size_t)b * box_rows * kP)),
             "l"(tmap), "r"(s0 - 4), "r"(b * box_rows), "r"(smem_u32(bar))
             : "memory");
+      // f_n of the tile is read only by the final RK combination: start
+      // bringing it into L2 now
+      if (fnmap && stage != 0)
+        for (int b = 0; b < nbox; ++b)
+          asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                           fnmap),
+                       "r"(s0), "r"(b * box_rows)
+                       : "memory");
     }
     __syncthreads();  // the barrier is initialised before anyone polls it
+    copy_weights();   // while the boxes are in flight
     uint32_t ok = 0;
     for (int it = 0; it < (1 << 22) && !ok; ++it) {
       asm volatile(
@@ -334,6 +348,7 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
       tile[v * kP + c] = val;
     }
   }
+  if (!(interior && tmap)) copy_weights();
   __syncthreads();
 
   const bool collide = g.tau_mode != kTauNone;
@@ -360,7 +375,7 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
             const float e[4] = {x.x, x.y, x.z, x.w};
             float w[5];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) w[q] = tb.mw[q * V + v];
+            for (int q = 0; q < 5; ++q) w[q] = mws[q * V + v];
 #pragma unroll
             for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -554,10 +569,11 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
 __global__ void __launch_bounds__(kNT, kMinCtas)
 sod32_stage_kernel(const float* __restrict__ fin, const float* __restrict__ fn, float* fout,
                    int stage, int* err, SodGeom g, SodTables<float> tb, const int* __restrict__ rowv,
-                   int nneg, const __grid_constant__ CUtensorMap tmap, int use_tma, int box_rows,
+                   int nneg, const __grid_constant__ CUtensorMap tmap,
+                   const __grid_constant__ CUtensorMap fnmap, int use_tma, int box_rows,
                    int nbox) {
   sod32_tile(fin, fn, fout, stage, err, g, tb, rowv, nneg, blockIdx.x * kB2,
-             use_tma ? &tmap : nullptr, box_rows, nbox, 0u);
+             use_tma ? &tmap : nullptr, use_tma ? &fnmap : nullptr, box_rows, nbox, 0u);
 }
 
 // Batched: a persistent grid walks the task list of all runs of one class
@@ -574,8 +590,8 @@ sod32_batch_kernel(const SodRunDesc<float>* __restrict__ runs, const SodTask* __
     float* fout = stage == 0 ? R.F1 : (stage == 1 ? R.F2 : R.F0);
     int nbox = 0;
     const int br = tma_box_rows_dev(R.g.V, &nbox);
-    sod32_tile(fin, R.F0, fout, stage, err, R.g, R.tb, R.rowv, R.nneg, tk.s0, nullptr, br, nbox,
-               0u);
+    sod32_tile(fin, R.F0, fout, stage, err, R.g, R.tb, R.rowv, R.nneg, tk.s0, nullptr, nullptr,
+               br, nbox, 0u);
     __syncthreads();
   }
 }
@@ -605,13 +621,14 @@ EncodeTiled encode_fn() {
 }
 
 // Tensor map of one population buffer: 2-D FP32 [V][Z] with row stride ldz,
-// box kC cells x box_rows rows, zero fill outside.
-bool make_map(CUtensorMap* m, const float* f, int Z, int ldz, int V, int box_rows) {
+// box box_cells cells x box_rows rows, zero fill outside.
+bool make_map(CUtensorMap* m, const float* f, int Z, int ldz, int V, int box_cells,
+              int box_rows) {
   EncodeTiled enc = encode_fn();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)Z, (cuuint64_t)V};
   const cuuint64_t strides[1] = {(cuuint64_t)ldz * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kC, (cuuint32_t)box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cells, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(f), dims, strides, box,
              es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -646,15 +663,18 @@ cudaError_t sod32_stage_launch(const SodGeom& g, const SodTables<float>& tb, con
   }
   int nbox = 0;
   const int br = tma_box_rows(g.V, &nbox);
-  CUtensorMap m;
+  CUtensorMap m, mn;
   std::memset(&m, 0, sizeof(m));
-  // TMA needs a 16-byte aligned base and row stride (cudaMalloc'd buffers,
+  std::memset(&mn, 0, sizeof(mn));
+  // TMA needs 16-byte aligned bases and row stride (cudaMalloc'd buffers,
   // ldz a multiple of 32) and at least one whole interior tile
   const bool tma = g.Z >= kB2 + 8 && (reinterpret_cast<uintptr_t>(fin) % 16) == 0 &&
-                   (g.ldz % 4) == 0 && make_map(&m, fin, g.Z, g.ldz, g.V, br);
+                   (reinterpret_cast<uintptr_t>(fn) % 16) == 0 && (g.ldz % 4) == 0 &&
+                   make_map(&m, fin, g.Z, g.ldz, g.V, kC, br) &&
+                   make_map(&mn, fn, g.Z, g.ldz, g.V, kB2, br);
   const int grid = (g.Z + kB2 - 1) / kB2;
   sod32_stage_kernel<<<grid, kNT, sod32_smem_bytes(g.V, g.QL), st>>>(
-      fin, fn, fout, stage, err, g, tb, rowv, nneg, m, tma ? 1 : 0, br, nbox);
+      fin, fn, fout, stage, err, g, tb, rowv, nneg, m, mn, tma ? 1 : 0, br, nbox);
   return cudaGetLastError();
 }
 
