@@ -698,6 +698,7 @@ struct SodClass {
   void* runs_dev;  // SodRunDesc<T>[nr]
   SodTask* tasks_dev;
   int ntasks;
+  void* maps_dev;  // packed FP32 kernel: 4 tensor maps per run, or NULL
 };
 
 struct rslb_sod_batch {
@@ -725,6 +726,7 @@ void batch_free(rslb_sod_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (auto& c : b->cls) {
     if (c.runs_dev) cudaFree(c.runs_dev);
+    if (c.maps_dev) cudaFree(c.maps_dev);
     if (c.tasks_dev) cudaFree(c.tasks_dev);
   }
   if (b->step_dev) cudaFree(b->step_dev);
@@ -740,7 +742,8 @@ cudaError_t batch_enqueue(rslb_sod_batch* b, int nsteps) {
       for (const SodClass& c : b->cls) {
         cudaError_t e = sod_batch_stage_launch<T>(
             c.B, c.smem, c.ctas_per_sm * b->nsm, (const SodRunDesc<T>*)c.runs_dev, c.tasks_dev,
-            c.ntasks, b->step_dev, stage, b->err, c.V, b->stream);
+            c.ntasks, b->step_dev, stage, b->err, c.V, b->stream,
+            c.B == kSod32Cells ? c.maps_dev : nullptr);
         if (e != cudaSuccess) return e;
       }
     batch_step_increment<<<1, 1, 0, b->stream>>>(b->step_dev);
@@ -803,6 +806,18 @@ int batch_build_classes(rslb_sod_batch* b, int autotune) {
       rd.push_back(d);
     }
     c.smem = 0;
+    // tensor maps of every run for the packed FP32 kernel's bulk-tensor staging
+    if constexpr (sizeof(T) == 4) {
+      const size_t mb = sod32_map_bytes();
+      std::vector<unsigned char> maps(4 * mb * rd.size());
+      bool ok = true;
+      for (size_t q = 0; q < rd.size() && ok; ++q)
+        ok = sod32_make_maps(maps.data() + 4 * mb * q, (const float*)rd[q].F0,
+                             (const float*)rd[q].F1, (const float*)rd[q].F2, rd[q].g.Z,
+                             rd[q].g.ldz, V);
+      if (ok && cudaMalloc(&c.maps_dev, maps.size()) == cudaSuccess)
+        cudaMemcpy(c.maps_dev, maps.data(), maps.size(), cudaMemcpyHostToDevice);
+    }
     auto make_tasks = [&](int B) {
       tasks.clear();
       for (size_t q = i; q < j; ++q) {
@@ -854,11 +869,13 @@ int batch_build_classes(rslb_sod_batch* b, int autotune) {
           cudaEventCreate(&e1);
           // stage 0 reads F0 and writes F1 only: safe to repeat
           sod_batch_stage_launch<T>(B, smem, k * b->nsm, (const SodRunDesc<T>*)c.runs_dev, td,
-                                    (int)tasks.size(), b->step_dev, 0, b->err, V, b->stream);
+                                    (int)tasks.size(), b->step_dev, 0, b->err, V, b->stream,
+                                    B == kSod32Cells ? c.maps_dev : nullptr);
           cudaEventRecord(e0, b->stream);
           for (int rep = 0; rep < 3; ++rep)
             sod_batch_stage_launch<T>(B, smem, k * b->nsm, (const SodRunDesc<T>*)c.runs_dev, td,
-                                      (int)tasks.size(), b->step_dev, 0, b->err, V, b->stream);
+                                      (int)tasks.size(), b->step_dev, 0, b->err, V, b->stream,
+                                      B == kSod32Cells ? c.maps_dev : nullptr);
           cudaEventRecord(e1, b->stream);
           cudaEventSynchronize(e1);
           cudaEventElapsedTime(&ms, e0, e1);

@@ -154,9 +154,19 @@ __device__ __forceinline__ T weno_corr(T D0, T D1, T D2, T D3, T K1, T K2, T K3)
   // Values below the smallest normal number count as zero: the FP32 reciprocal
   // flushes subnormal inputs, and a vanishing denominator means the
   // correction vanishes (limit rules).
+  // The indicators are scaled by the power of two at or below their maximum
+  // (the weights are homogeneous in sigma; the scaling only keeps the fourth
+  // powers in range), formed from the exponent bits instead of a reciprocal.
   const T tiny = Prec<T>::tiny();
   const T smax = fmax(s1, fmax(s2, s3));
-  const T inv = smax > tiny ? fast_rcp(smax) : T(0);
+  T inv = T(0);
+  if (smax > tiny) {
+    if constexpr (sizeof(T) == 4)
+      inv = __int_as_float((254 - ((__float_as_int(smax) >> 23) & 0xff)) << 23);
+    else
+      inv = __longlong_as_double((long long)(2046 - ((__double_as_longlong(smax) >> 52) & 0x7ff))
+                                 << 52);
+  }
   const T r1 = s1 * inv, r2 = s2 * inv, r3 = s3 * inv;
   const T t1 = r1 * r1, t2 = r2 * r2, t3 = r3 * r3;
   const T n1 = T(0.1) * (t2 * t3), n2 = T(0.6) * (t1 * t3), n3 = T(0.3) * (t1 * t2);
@@ -692,16 +702,18 @@ size_t sod_stage_smem_bytes(bool fp64, int B, int V, int QL, int nm) {
 
 cudaError_t sod32_batch_launch(size_t smem, int grid, const SodRunDesc<float>* runs,
                                const SodTask* tasks, int ntasks, const long long* step, int stage,
-                               int* err, cudaStream_t st);
+                               int* err, const void* maps, cudaStream_t st);
 
 // Batched stages: all runs of a class share V (so nseg and the tile width).
 template <typename T>
 cudaError_t sod_batch_stage_launch(int B, size_t smem, int grid, const SodRunDesc<T>* runs,
                                    const SodTask* tasks, int ntasks, const long long* step,
-                                   int stage, int* err, int V, cudaStream_t st) {
+                                   int stage, int* err, int V, cudaStream_t st,
+                                   const void* maps) {
   if (ntasks == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (B == kSod32Cells) return sod32_batch_launch(smem, grid, runs, tasks, ntasks, step, stage, err, st);
+    if (B == kSod32Cells)
+      return sod32_batch_launch(smem, grid, runs, tasks, ntasks, step, stage, err, maps, st);
     if (B == 32) {
       sod_batch_kernel<T, 32, 320><<<grid, 320, smem, st>>>(runs, tasks, ntasks, step, stage, err,
                                                            pick_nseg(V, 32, 320, 4));
@@ -729,10 +741,10 @@ cudaError_t sod_batch_stage_launch(int B, size_t smem, int grid, const SodRunDes
 
 template cudaError_t sod_batch_stage_launch<float>(int, size_t, int, const SodRunDesc<float>*,
                                                    const SodTask*, int, const long long*, int,
-                                                   int*, int, cudaStream_t);
+                                                   int*, int, cudaStream_t, const void*);
 template cudaError_t sod_batch_stage_launch<double>(int, size_t, int, const SodRunDesc<double>*,
                                                     const SodTask*, int, const long long*, int,
-                                                    int*, int, cudaStream_t);
+                                                    int*, int, cudaStream_t, const void*);
 
 // ---------------------------------------------------------------------------
 // Initialisation: per-cell FP64 coefficients, then populations.

@@ -83,6 +83,12 @@ cudaError_t sod_set_attributes();
 constexpr int kSod32Cells = RSLB_PACKED_TILE_CELLS;
 constexpr int kSod32Threads = 8 * kSod32Cells;
 
+// Tensor maps for batched packed-kernel launches (bytes per map; four maps
+// per run: F0, F1, F2 with 36-cell boxes, F0 with tile-wide boxes).
+size_t sod32_map_bytes();
+bool sod32_make_maps(void* out4, const float* F0, const float* F1, const float* F2, int Z,
+                     int ldz, int V);
+
 cudaError_t sod32_set_attributes();
 
 // Pick the tile width for V velocities; returns B = 0 if V does not fit.
@@ -108,7 +114,8 @@ cudaError_t sod32_stage_launch(const SodGeom& g, const SodTables<float>& tb, con
 template <typename T>
 cudaError_t sod_batch_stage_launch(int B, size_t smem, int grid, const SodRunDesc<T>* runs,
                                    const SodTask* tasks, int ntasks, const long long* step,
-                                   int stage, int* err, int V, cudaStream_t st);
+                                   int stage, int* err, int V, cudaStream_t st,
+                                   const void* maps = nullptr);
 size_t sod_stage_smem_bytes(bool fp64, int B, int V, int QL, int nm);
 
 // Per-cell coefficients c''_{k,m} (FP64) of f^eq for given (n, T, beta) per

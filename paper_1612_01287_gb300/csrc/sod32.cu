@@ -69,9 +69,16 @@ __device__ __forceinline__ float2 weno_corr2(float2 D0, float2 D1, float2 D2, fl
   const float2 h1 = fma2(splat(0.5f), D1, mul2(splat(-0.2f), D0));
   const float2 h2 = fma2(splat(1.2f), D2, mul2(splat(0.6f), D1));
   const float2 h3 = fma2(splat(1.2f), D2, mul2(splat(-0.3f), D3));
+  // scale the smoothness indicators by the power of two at or below their
+  // maximum (the weights are homogeneous in sigma; this only keeps the
+  // fourth powers inside the FP32 range): integer exponent arithmetic
+  // instead of a reciprocal
   const float mx = fmaxf(s1.x, fmaxf(s2.x, s3.x));
   const float my = fmaxf(s1.y, fmaxf(s2.y, s3.y));
-  const float2 inv = make_float2(mx > tiny ? rcp_approx(mx) : 0.f, my > tiny ? rcp_approx(my) : 0.f);
+  auto inv_pow2 = [&](float m) {
+    return m > tiny ? __int_as_float((254 - ((__float_as_int(m) >> 23) & 0xff)) << 23) : 0.f;
+  };
+  const float2 inv = make_float2(inv_pow2(mx), inv_pow2(my));
   const float2 r1 = mul2(s1, inv), r2 = mul2(s2, inv), r3 = mul2(s3, inv);
   const float2 t1 = mul2(r1, r1), t2 = mul2(r2, r2), t3 = mul2(r3, r3);
   const float2 p23 = mul2(t2, t3), p13 = mul2(t1, t3), p12 = mul2(t1, t2);
@@ -249,7 +256,7 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
                                            int* err, const SodGeom& g, const SodTables<float>& tb,
                                            const int* __restrict__ rowv, int nneg, int s0,
                                            const CUtensorMap* tmap, const CUtensorMap* fnmap,
-                                           int box_rows, int nbox, uint32_t phase) {
+                                           int box_rows, int nbox, int& bar_uses) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
   const int V = g.V;
@@ -274,10 +281,14 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
   // ---- 1. stage rows: cell s0-4+p goes to position p (0 <= p < kC) ----
   const bool interior = (s0 - 4 >= 0) && (s0 + kB2 + 4 <= g.Z);
   if (interior && tmap) {
-    // one thread issues the box copies; everyone waits on the mbarrier
+    // one thread issues the box copies; everyone waits on the mbarrier (set
+    // up at the CTA's first bulk-copied tile, one phase per tile after that)
+    const uint32_t phase = (uint32_t)(bar_uses & 1);
     if (tid == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      if (bar_uses == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       const uint32_t bytes = (uint32_t)(nbox * box_rows * kP * sizeof(float));
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
@@ -311,6 +322,7 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
       if (!ok && it > 32) __nanosleep(32);
     }
     if (!ok && tid == 0) report_err(err, 97, s0);
+    ++bar_uses;
   } else if (interior) {
     // eight 16-byte loads in flight per thread before the shared-memory stores
     const float* src = fin + s0 - 4;
@@ -572,16 +584,21 @@ sod32_stage_kernel(const float* __restrict__ fin, const float* __restrict__ fn, 
                    int nneg, const __grid_constant__ CUtensorMap tmap,
                    const __grid_constant__ CUtensorMap fnmap, int use_tma, int box_rows,
                    int nbox) {
+  int bar_uses = 0;
   sod32_tile(fin, fn, fout, stage, err, g, tb, rowv, nneg, blockIdx.x * kB2,
-             use_tma ? &tmap : nullptr, use_tma ? &fnmap : nullptr, box_rows, nbox, 0u);
+             use_tma ? &tmap : nullptr, use_tma ? &fnmap : nullptr, box_rows, nbox, bar_uses);
 }
 
-// Batched: a persistent grid walks the task list of all runs of one class
-// (plain-load staging).
+// Batched: a persistent grid walks the task list of all runs of one class.
+// maps (optional): per run, the tensor maps of F0, F1, F2 (36-cell boxes) and
+// of F0 with tile-wide boxes for the f_n prefetch; without them the tiles
+// are staged by plain loads.
 __global__ void __launch_bounds__(kNT, kMinCtas)
 sod32_batch_kernel(const SodRunDesc<float>* __restrict__ runs, const SodTask* __restrict__ tasks,
-                   int ntasks, const long long* __restrict__ step, int stage, int* err) {
+                   int ntasks, const long long* __restrict__ step, int stage, int* err,
+                   const CUtensorMap* __restrict__ maps) {
   const long long n = *step;
+  int bar_uses = 0;
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const SodTask tk = tasks[t];
     const SodRunDesc<float>& R = runs[tk.run];
@@ -590,8 +607,10 @@ sod32_batch_kernel(const SodRunDesc<float>* __restrict__ runs, const SodTask* __
     float* fout = stage == 0 ? R.F1 : (stage == 1 ? R.F2 : R.F0);
     int nbox = 0;
     const int br = tma_box_rows_dev(R.g.V, &nbox);
-    sod32_tile(fin, R.F0, fout, stage, err, R.g, R.tb, R.rowv, R.nneg, tk.s0, nullptr, nullptr,
-               br, nbox, 0u);
+    const CUtensorMap* tm = maps ? maps + (size_t)tk.run * 4 + stage : nullptr;
+    const CUtensorMap* fm = maps ? maps + (size_t)tk.run * 4 + 3 : nullptr;
+    sod32_tile(fin, R.F0, fout, stage, err, R.g, R.tb, R.rowv, R.nneg, tk.s0, tm, fm, br, nbox,
+               bar_uses);
     __syncthreads();
   }
 }
@@ -639,9 +658,24 @@ bool make_map(CUtensorMap* m, const float* f, int Z, int ldz, int V, int box_cel
 
 cudaError_t sod32_batch_launch(size_t smem, int grid, const SodRunDesc<float>* runs,
                                const SodTask* tasks, int ntasks, const long long* step, int stage,
-                               int* err, cudaStream_t st) {
-  sod32_batch_kernel<<<grid, kNT, smem, st>>>(runs, tasks, ntasks, step, stage, err);
+                               int* err, const void* maps, cudaStream_t st) {
+  sod32_batch_kernel<<<grid, kNT, smem, st>>>(runs, tasks, ntasks, step, stage, err,
+                                              static_cast<const CUtensorMap*>(maps));
   return cudaGetLastError();
+}
+
+size_t sod32_map_bytes() { return sizeof(CUtensorMap); }
+
+// The four tensor maps of one run (see sod32_batch_kernel); false if the
+// encoder is not available or a map cannot be built.
+bool sod32_make_maps(void* out4, const float* F0, const float* F1, const float* F2, int Z,
+                     int ldz, int V) {
+  if (Z < kB2 + 8 || (ldz % 4) != 0) return false;
+  int nbox = 0;
+  const int br = tma_box_rows(V, &nbox);
+  CUtensorMap* m = static_cast<CUtensorMap*>(out4);
+  return make_map(&m[0], F0, Z, ldz, V, kC, br) && make_map(&m[1], F1, Z, ldz, V, kC, br) &&
+         make_map(&m[2], F2, Z, ldz, V, kC, br) && make_map(&m[3], F0, Z, ldz, V, kB2, br);
 }
 
 cudaError_t sod32_set_attributes() {
