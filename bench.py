@@ -64,6 +64,22 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's time (every rank gets it); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Units all ranks processed (each rank its own replica) per second of the
+    slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def workload_dt(w):
     from paper_1612_01287_gb300 import quadrature
     xi, _, _, _ = quadrature(w["Q_xi"], w["Q_L"])
@@ -452,10 +468,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = clk.stop()
     ms = start.elapsed_time(end)
     per_tube_step_ms = [ev[j].elapsed_time(ev[j + 1]) for j in range(nev)]
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     for t in tubes:
         t.sync()
 
@@ -475,11 +488,8 @@ def run_ours(args, rank, world, local_rank):
         tube.moments_into(host_m.data_ptr())
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_val = world * V * Z * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e_val = whole_job_rate(world, V * Z * e2e_steps, e2e_s)
 
     # ---- FP64 path, one tube, a few steps (ALU-bound on this part) ----
     fp64 = None
@@ -518,7 +528,7 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return 0
 
-    value = world * cv_per_step * args.steps / (ms * 1e-3)
+    value = whole_job_rate(world, cv_per_step * args.steps, ms * 1e-3)
     per_launch_ms = statistics.mean(per_tube_step_ms) / 3.0
     peak, peak_kind = measured_peak()
     achieved = BYTES_PER_CV_STEP_F32 / 3.0 * V * Z / (per_launch_ms * 1e-3) / 1e9
