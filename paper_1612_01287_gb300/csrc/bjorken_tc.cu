@@ -39,7 +39,7 @@ constexpr int kTcWorkers = 128;
 constexpr uint32_t kATile = 128 * 128;  // bytes: 128 rows x 32 FP32
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kErrTimeout = 97;
-constexpr int kTcMaxRowsPerWarp = 20;  // MMA N <= 80: state rows per warp in a K-block
+constexpr int kTcMaxRowsPerWarp = kTcMaxCols / 4;  // state rows per warp in a K-block
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
