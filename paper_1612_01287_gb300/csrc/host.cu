@@ -632,9 +632,12 @@ extern "C" int rslb_get_state(rslb_handle* h, void* f, int on_device) {
   clear_error();
   if (!h || !f) return set_error(RSLB_ERR_ARG, "rslb_get_state: NULL argument");
   const size_t es = h->fp64 ? sizeof(double) : sizeof(float);
-  cudaError_t e = cudaMemcpy2DAsync(f, es * h->cfg.Z, h->F[0], es * h->ldz, es * h->cfg.Z, h->V,
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                    h->stream);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  // one linear copy when the rows are not padded
+  cudaError_t e = h->ldz == h->cfg.Z
+                      ? cudaMemcpyAsync(f, h->F[0], es * (size_t)h->cfg.Z * h->V, kind, h->stream)
+                      : cudaMemcpy2DAsync(f, es * h->cfg.Z, h->F[0], es * h->ldz, es * h->cfg.Z,
+                                          h->V, kind, h->stream);
   if (e != cudaSuccess) return cuda_error(e, "rslb_get_state: copy");
   return check_device_error(h);
 }
@@ -643,9 +646,11 @@ extern "C" int rslb_set_state(rslb_handle* h, const void* f, int on_device) {
   clear_error();
   if (!h || !f) return set_error(RSLB_ERR_ARG, "rslb_set_state: NULL argument");
   const size_t es = h->fp64 ? sizeof(double) : sizeof(float);
-  cudaError_t e = cudaMemcpy2DAsync(h->F[0], es * h->ldz, f, es * h->cfg.Z, es * h->cfg.Z, h->V,
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                    h->stream);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = h->ldz == h->cfg.Z
+                      ? cudaMemcpyAsync(h->F[0], f, es * (size_t)h->cfg.Z * h->V, kind, h->stream)
+                      : cudaMemcpy2DAsync(h->F[0], es * h->ldz, f, es * h->cfg.Z, es * h->cfg.Z,
+                                          h->V, kind, h->stream);
   if (e != cudaSuccess) return cuda_error(e, "rslb_set_state: copy");
   return RSLB_OK;
 }

@@ -54,13 +54,16 @@ def test_contraction_against_fp64(QL):
     assert worst < 2e-5
 
 
-def test_mixed_batch_parity_tf32x3():
+@pytest.mark.parametrize("QL", [2, 3, 4])
+def test_mixed_batch_parity_tf32x3(QL):
+    """Q_L = 2 is the paper's radial set; 3 the workload's; 4 the largest the
+    tensor-core epilogue takes."""
     from paper_1612_01287_gb300 import Bjorken
     Qs, gases, taus = MIXED
-    with Bjorken(Qs, gases, taus, Q_L=3, precision="f32", kp_mode="tf32x3", dtau=1e-2) as b:
+    with Bjorken(Qs, gases, taus, Q_L=QL, precision="f32", kp_mode="tf32x3", dtau=1e-2) as b:
         b.step(60)
         got = b.read()
-    ref, _ = oracle_batch(Qs, gases, taus, 60)
+    ref, _ = oracle_batch(Qs, gases, taus, 60, Q_L=QL)
     e = errors(got, ref)
     print("tf32x3", e)
     for k, v in e.items():

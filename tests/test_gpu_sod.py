@@ -11,9 +11,8 @@ import pytest
 
 import oracle
 from paper_1612_01287_gb300 import workloads
+from paper_1612_01287_gb300._lib import PACKED_TILE_CELLS as PACKED
 from tests import sodcase
-
-from paper_1612_01287_gb300._lib import PACKED_TILE_CELLS as PACKED  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -248,3 +247,19 @@ def test_graph_captured_steps_match_plain_launches():
         ref39 = c.get_state()
     np.testing.assert_array_equal(got, ref39)
     assert not np.array_equal(ref, ref39)
+
+
+@pytest.mark.parametrize("bc", ["fixed_eq", "periodic", "outflow"])
+@pytest.mark.parametrize("precision,tol", [("f32", TOL32), ("f64", TOL64)])
+def test_boundary_tiles_at_many_velocities(bc, precision, tol):
+    """150 velocities (the packed FP32 kernel, bulk-tensor staging of the
+    interior tiles) on 130 cells: interior tiles, both boundary tiles with each
+    boundary rule, and a ragged last tile."""
+    from paper_1612_01287_gb300 import Sod
+    n, T, b = workloads.random_smooth_fields(130, beta_max=0.4)
+    case = dict(Z=130, Q_xi=50, Q_L=3, N_Omega=5, bc=bc, tau=5e-3, dt=1e-3, fields=(n, T, b))
+    if precision == "f32":
+        with Sod(precision="f32", **sodcase.gpu_kwargs(case)) as s:
+            assert s.launch_info()[0] == PACKED
+    errs = sodcase.compare(case, 20, precision, tol)
+    print(bc, precision, errs)
