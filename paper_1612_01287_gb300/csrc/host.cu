@@ -218,6 +218,7 @@ struct rslb_handle {
   double* d_p;
   double* d_wp;
   double* d_L1k;
+  void* d_mom;  // output-moment weights (sod_moment_weights)
   int* d_err;
   double* d_fields;
   double t;
@@ -264,7 +265,7 @@ void free_handle(rslb_handle* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   void* ptrs[] = {h->F[0], h->F[1], h->F[2], h->t_mw, h->t_xi, h->t_wp, h->t_L1k, h->t_gL,
                   h->t_gR, h->t_kidx, h->t_rowv, h->t_gl_t, h->t_gl_w, h->d_xi, h->d_p, h->d_wp,
-                  h->d_L1k, h->d_err, h->d_fields};
+                  h->d_L1k, h->d_mom, h->d_err, h->d_fields};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -433,6 +434,14 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
   if (!rc) rc = upload<double>((void**)&h->d_p, pv);
   if (!rc) rc = upload<double>((void**)&h->d_wp, wp);
   if (!rc) rc = upload<double>((void**)&h->d_L1k, L1k);
+  if (!rc) {
+    std::vector<unsigned char> mom(sod_moment_weights(fp64, V, xiv.data(), pv.data(), nullptr));
+    sod_moment_weights(fp64, V, xiv.data(), pv.data(), mom.data());
+    if (cudaMalloc(&h->d_mom, mom.size()) != cudaSuccess)
+      rc = set_error(RSLB_ERR_ALLOC, "cudaMalloc of a table failed");
+    else if (cudaMemcpy(h->d_mom, mom.data(), mom.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = set_error(RSLB_ERR_CUDA, "copying a table to the device failed");
+  }
   const size_t es = fp64 ? sizeof(double) : sizeof(float);
   const size_t fbytes = es * (size_t)V * h->ldz;
   for (int i = 0; i < 3 && !rc; ++i) {
@@ -613,10 +622,10 @@ extern "C" int rslb_sync(rslb_handle* h) {
 extern "C" int rslb_moments(rslb_handle* h, double* out, int out_on_device) {
   clear_error();
   if (!h || !out) return set_error(RSLB_ERR_ARG, "rslb_moments: NULL argument");
-  cudaError_t e = h->fp64 ? sod_moments_launch<double>(h->geom, tables64_of(h),
+  cudaError_t e = h->fp64 ? sod_moments_launch<double>(h->geom, h->d_mom,
                                                        (const double*)h->F[0], h->d_fields,
                                                        h->d_err, h->stream)
-                          : sod_moments_launch<float>(h->geom, tables64_of(h),
+                          : sod_moments_launch<float>(h->geom, h->d_mom,
                                                       (const float*)h->F[0], h->d_fields,
                                                       h->d_err, h->stream);
   if (e != cudaSuccess) return cuda_error(e, "rslb_moments: launch");

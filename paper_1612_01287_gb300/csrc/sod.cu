@@ -819,61 +819,4 @@ template cudaError_t sod_init_launch<double>(const SodGeom&, const SodTablesF64&
                                              const double*, const double*, double*, double*,
                                              int*, cudaStream_t);
 
-// ---------------------------------------------------------------------------
-// Output moments: one warp per cell, FP64 sums.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void sod_moments_kernel(SodGeom g, SodTablesF64 tb, const T* __restrict__ f,
-                                   double* out, int* err) {
-  const int warps = blockDim.x >> 5;
-  const int s = blockIdx.x * warps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (s >= g.Z) return;
-  double S[10];
-#pragma unroll
-  for (int q = 0; q < 10; ++q) S[q] = 0.0;
-  for (int v = lane; v < g.V; v += 32) {
-    const double x = (double)f[(size_t)v * g.ldz + s];
-    const double xi = tb.xi[v], p = tb.p[v];
-    S[0] += x;
-    S[1] += x * xi;
-    S[2] += x * p;
-    S[3] += x * p * xi;
-    S[4] += x * p * xi * xi;
-    S[5] += x * (1.0 + xi);
-    S[6] += x * (1.0 - xi);
-    S[7] += x * p * (1.0 + xi) * (1.0 + xi);
-    S[8] += x * p * (1.0 - xi) * (1.0 - xi);
-    S[9] += x * p * (1.0 - xi) * (1.0 + xi);
-  }
-#pragma unroll
-  for (int q = 0; q < 10; ++q) S[q] = warp_sum(S[q]);
-  if (lane != 0) return;
-  const LandauOut L = landau_factored(S[5], S[6], S[7], S[8], S[9]);
-  if (!L.ok) report_error(err, 6, s);
-  const size_t Z = g.Z;
-  out[0 * Z + s] = L.n;
-  out[1 * Z + s] = L.E;
-  out[2 * Z + s] = L.E / 3.0;
-  out[3 * Z + s] = L.T;
-  out[4 * Z + s] = L.beta;
-  out[5 * Z + s] = L.gamma;
-  out[6 * Z + s] = L.n / (L.T * L.T * L.T);
-  out[7 * Z + s] = -4.0 * L.T * (S[1] - L.n * L.beta * L.gamma);
-  out[8 * Z + s] = 2.0 * L.E / 3.0 - S[9];
-  for (int q = 0; q < 5; ++q) out[(9 + q) * Z + s] = S[q];
-}
-
-template <typename T>
-cudaError_t sod_moments_launch(const SodGeom& g, const SodTablesF64& tb, const T* f,
-                               double* out, int* err, cudaStream_t st) {
-  sod_moments_kernel<T><<<(g.Z + 7) / 8, 256, 0, st>>>(g, tb, f, out, err);
-  return cudaGetLastError();
-}
-
-template cudaError_t sod_moments_launch<float>(const SodGeom&, const SodTablesF64&, const float*,
-                                               double*, int*, cudaStream_t);
-template cudaError_t sod_moments_launch<double>(const SodGeom&, const SodTablesF64&,
-                                                const double*, double*, int*, cudaStream_t);
-
 }  // namespace rslb

@@ -125,9 +125,17 @@ cudaError_t sod_init_launch(const SodGeom& g, const SodTablesF64& tb, const doub
                             const double* Tt, const double* beta, double* coef_scratch, T* f,
                             int* err, cudaStream_t st);
 
-// 14 FP64 fields per cell (rslb.h order), out[field*Z + s].
+// 14 FP64 fields per cell (rslb.h order), out[field*Z + s] (moments.cu).
+// w: per-velocity weight table of sod_moment_weights.
 template <typename T>
-cudaError_t sod_moments_launch(const SodGeom& g, const SodTablesF64& tb, const T* f,
-                               double* out, int* err, cudaStream_t st);
+cudaError_t sod_moments_launch(const SodGeom& g, const void* w, const T* f, double* out,
+                               int* err, cudaStream_t st);
+
+// Host: the moment weight table, for velocity v w_q = (1+xi), (1-xi),
+// p(1+xi)^2, p(1-xi)^2, p(1-xi^2): FP32 populations get 12 floats per
+// velocity {hi0..hi3}{hi4 lo0 lo1 lo2}{lo3 lo4 0 0} with w = hi + lo; FP64
+// populations get 6 doubles {w0..w4 0}.  With out == NULL only the byte
+// size is returned.
+size_t sod_moment_weights(bool fp64, int V, const double* xi, const double* p, void* out);
 
 }  // namespace rslb

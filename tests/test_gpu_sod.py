@@ -263,3 +263,37 @@ def test_boundary_tiles_at_many_velocities(bc, precision, tol):
             assert s.launch_info()[0] == PACKED
     errs = sodcase.compare(case, 20, precision, tol)
     print(bc, precision, errs)
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-13), ("f32", 1e-12)])
+@pytest.mark.parametrize("Z,Q_xi", [(1000, 50), (77, 7)])
+def test_output_moments_of_a_given_state(precision, tol, Z, Q_xi):
+    """rslb_moments on a state loaded with rslb_set_state equals the oracle's
+    moments and Landau matching (Eq. macro_jk, Eqs. E_landau-pi_val) of the
+    same stored values.  The FP32 path sums exact products as double-floats,
+    so it is held to FP64-level agreement too.  Z is not a multiple of the
+    block width and the velocity chunks are uneven."""
+    from paper_1612_01287_gb300 import Sod
+    rng = np.random.default_rng(20261203 + Z)
+    zc = np.linspace(-1.0, 1.0, Z)
+    n = 1.0 + 0.5 * np.sin(3.0 * zc)
+    T = 0.8 + 0.3 * np.cos(2.0 * zc)
+    beta = 0.7 * np.sin(5.0 * zc)  # at |beta| = 0.9 the truncated f^eq is too negative
+    # for the noisy state below to stay physical
+    case = dict(Z=Z, Q_xi=Q_xi, Q_L=3, bc="outflow", tau=1e-2, dt=1e-4)
+    p = sodcase.oracle_params(case)
+    f = oracle.sod_init_fields(p, n, T, beta)  # oracle layout [Z][V]
+    f = f * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, f.shape))  # off equilibrium: Pi, q != 0
+    with Sod(precision=precision, fields=(n, T, beta), **case) as s:
+        s.set_state(f.T)  # library layout [V][Z]
+        stored = s.get_state().astype(np.float64)
+        mg = s.moments()
+    mo = oracle.sod_moments(p, np.ascontiguousarray(stored.T))
+    # q = -4T(N^z - n beta gamma) and Pi = 2E/3 - D are differences of nearly
+    # equal terms: their rounding is measured against the size of those terms
+    scale = {k: np.abs(mo[k]).max() for k in oracle.SOD_FIELDS}
+    scale["q"] = np.abs(4.0 * mo["T"] * mo["Nz"]).max()
+    scale["Pi"] = np.abs(mo["E"]).max()
+    for k in oracle.SOD_FIELDS:
+        err = np.abs(mg[k] - mo[k]).max() / scale[k]
+        assert err <= tol, (k, err)
