@@ -10,13 +10,11 @@
 // accesses of 8 consecutive rows hit distinct banks); "slot" s of the sweep
 // is the pair (position s, position s + kH).  Interior tiles are brought in
 // by tensor-memory-access bulk copies (cp.async.bulk.tensor, one box per
-// block of at most 128 rows, each completing on its own mbarrier, so the
-// moment reduction of a box overlaps the flight of the next), boundary tiles
-// by plain loads.  The rest of the stage -- moments (Kahan-compensated FP32
-// with an error-free FP32 warp reduction), FP64 Landau matching, the f^eq
+// block of rows, completion on an mbarrier), boundary tiles by plain loads.
+// The rest of the stage -- moments (Kahan-compensated FP32 with an
+// error-free FP32 warp reduction), FP64 Landau matching, the f^eq
 // coefficients, WENO5 in difference form, relaxation, RK update -- follows
-// the scalar kernel of sod.cu, except that each warp stores the rows it has
-// just swept (with the f_n term) before sweeping its next ones.
+// the scalar kernel of sod.cu.
 #include <cuda.h>
 
 #include <cstring>
@@ -37,7 +35,7 @@ constexpr int kNT = kSod32Threads; // a warp per 4 cells in the moments, 8 threa
 constexpr int kMinCtas = kB2 <= 20 ? 3 : 2;  // CTAs per SM the registers are sized for
 static_assert(kB2 % 4 == 0 && kH % 2 == 0 && (kC / 4) % 2 == 1, "packed tile shape");
 constexpr int kMP = 8;          // coefficient pitch (m) for N_Omega <= 7
-constexpr int kInflight = 8;    // 16-byte global loads in flight per thread (plain staging)
+constexpr int kInflight = 8;    // 16-byte global loads in flight per thread (staging, store)
 
 __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -213,14 +211,8 @@ __device__ __forceinline__ void sweep_row2(float* row, float xi, const float2* w
   }
 }
 
-// Rows of the tile come in nbox boxes of at most kBoxRows rows (a multiple
-// of 8), each completing on its own mbarrier, so the moment reduction starts
-// on the first box while the later ones are in flight.
-constexpr int kBoxRows = 128;
-constexpr int kMaxBoxes = 16;  // mbarriers in the 128-byte barrier block
-
 __device__ __forceinline__ int tma_box_rows_dev(int V, int* nbox) {
-  const int nb = (V + kBoxRows - 1) / kBoxRows;
+  const int nb = (V + 255) / 256;
   int r = (V + nb - 1) / nb;
   r = (r + 7) / 8 * 8;
   *nbox = nb;
@@ -235,10 +227,10 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 
 // Shared memory: tile [rows][kP] floats (rows = V rounded up to whole TMA
 // boxes), then partial moments, cell scalars, coefficients
-// [QL][kH][kMP][2] floats, gco [kH][4] floats, the mbarriers of the boxes
-// and the five moment weights of every velocity [5][V].
+// [QL][kH][kMP][2] floats, gco [kH][4] floats, an mbarrier and the five
+// moment weights of every velocity [5][V].
 static int tma_box_rows(int V, int* nbox) {
-  const int nb = (V + kBoxRows - 1) / kBoxRows;
+  const int nb = (V + 255) / 256;
   int r = (V + nb - 1) / nb;
   r = (r + 7) / 8 * 8;  // a box is 4 kC r bytes: a multiple of 128 B
   if (nbox) *nbox = nb;
@@ -288,46 +280,26 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
 
   // ---- 1. stage rows: cell s0-4+p goes to position p (0 <= p < kC) ----
   const bool interior = (s0 - 4 >= 0) && (s0 + kB2 + 4 <= g.Z);
-  const bool bulk = interior && tmap;
-  const uint32_t phase = (uint32_t)(bar_uses & 1);
-  // wait for box b (bounded; a timeout is reported and the tile goes on)
-  auto wait_box = [&](int b) {
-    uint32_t ok = 0;
-    for (int it = 0; it < (1 << 22) && !ok; ++it) {
-      asm volatile(
-          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-          " selp.u32 %0, 1, 0, p;\n}"
-          : "=r"(ok)
-          : "r"(smem_u32(bar + b)), "r"(phase)
-          : "memory");
-      if (!ok && it > 32) __nanosleep(32);
-    }
-    if (!ok) report_err(err, 97, s0);
-  };
-  if (bulk) {
-    // one thread issues the box copies, each completing on its own mbarrier
-    // (set up at the CTA's first bulk-copied tile, one phase per tile after
-    // that)
+  if (interior && tmap) {
+    // one thread issues the box copies; everyone waits on the mbarrier (set
+    // up at the CTA's first bulk-copied tile, one phase per tile after that)
+    const uint32_t phase = (uint32_t)(bar_uses & 1);
     if (tid == 0) {
       if (bar_uses == 0) {
-        for (int b = 0; b < nbox; ++b)
-          asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + b))
-                       : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      const uint32_t bytes = (uint32_t)(box_rows * kP * sizeof(float));
-      for (int b = 0; b < nbox; ++b) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                         smem_u32(bar + b)),
-                     "r"(bytes)
-                     : "memory");
+      const uint32_t bytes = (uint32_t)(nbox * box_rows * kP * sizeof(float));
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                   "r"(bytes)
+                   : "memory");
+      for (int b = 0; b < nbox; ++b)
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(tile + (size_t)b * box_rows * kP)),
-            "l"(tmap), "r"(s0 - 4), "r"(b * box_rows), "r"(smem_u32(bar + b))
+            "l"(tmap), "r"(s0 - 4), "r"(b * box_rows), "r"(smem_u32(bar))
             : "memory");
-      }
       // f_n of the tile is read only by the final RK combination: start
       // bringing it into L2 now
       if (fnmap && stage != 0)
@@ -337,8 +309,19 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
                        "r"(s0), "r"(b * box_rows)
                        : "memory");
     }
-    __syncthreads();  // the barriers are initialised before anyone polls them
+    __syncthreads();  // the barrier is initialised before anyone polls it
     copy_weights();   // while the boxes are in flight
+    uint32_t ok = 0;
+    for (int it = 0; it < (1 << 22) && !ok; ++it) {
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(ok)
+          : "r"(smem_u32(bar)), "r"(phase)
+          : "memory");
+      if (!ok && it > 32) __nanosleep(32);
+    }
+    if (!ok && tid == 0) report_err(err, 97, s0);
     ++bar_uses;
   } else if (interior) {
     // eight 16-byte loads in flight per thread before the shared-memory stores
@@ -377,12 +360,10 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
       tile[v * kP + c] = val;
     }
   }
-  if (!bulk) copy_weights();
+  if (!(interior && tmap)) copy_weights();
   __syncthreads();
 
   const bool collide = g.tau_mode != kTauNone;
-  if (bulk && !collide)
-    for (int b = 0; b < nbox; ++b) wait_box(b);
   if (collide) {
     // ---- 2. moments: warp w owns cells 4w .. 4w+3 of the tile, lanes own rows;
     //         blocks of four rows, Kahan-compensated across blocks ----
@@ -392,44 +373,36 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int q = 0; q < 5; ++q) { s[c][q] = 0.f; cpen[c][q] = 0.f; }
-      // rows box by box, each reduced as soon as it has landed (tiles staged
-      // by plain loads use the same grouping, so the sums do not depend on
-      // how the tile was staged)
-      for (int bx = 0; bx < nbox; ++bx) {
-        const int vb = bx * box_rows;
-        const int ve = min(V, vb + box_rows);
-        if (bulk) wait_box(bx);
-        for (int v0 = vb + lane; v0 < ve; v0 += 128) {
-          float blk[4][5];
+      for (int v0 = lane; v0 < V; v0 += 128) {
+        float blk[4][5];
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int q = 0; q < 5; ++q) blk[c][q] = 0.f;
+          for (int q = 0; q < 5; ++q) blk[c][q] = 0.f;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int v = v0 + 32 * u;
-            if (v < ve) {
-              const float4 x = *reinterpret_cast<const float4*>(tile + v * kP + 4 + 4 * warp);
-              const float e[4] = {x.x, x.y, x.z, x.w};
-              float w[5];
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + 32 * u;
+          if (v < V) {
+            const float4 x = *reinterpret_cast<const float4*>(tile + v * kP + 4 + 4 * warp);
+            const float e[4] = {x.x, x.y, x.z, x.w};
+            float w[5];
 #pragma unroll
-              for (int q = 0; q < 5; ++q) w[q] = mws[q * V + v];
+            for (int q = 0; q < 5; ++q) w[q] = mws[q * V + v];
 #pragma unroll
-              for (int c = 0; c < 4; ++c)
+            for (int c = 0; c < 4; ++c)
 #pragma unroll
-                for (int q = 0; q < 5; ++q) blk[c][q] = fmaf(e[c], w[q], blk[c][q]);
-            }
+              for (int q = 0; q < 5; ++q) blk[c][q] = fmaf(e[c], w[q], blk[c][q]);
           }
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-              const float y = blk[c][q] - cpen[c][q];
-              const float t = s[c][q] + y;
-              cpen[c][q] = (t - s[c][q]) - y;
-              s[c][q] = t;
-            }
         }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const float y = blk[c][q] - cpen[c][q];
+            const float t = s[c][q] + y;
+            cpen[c][q] = (t - s[c][q]) - y;
+            s[c][q] = t;
+          }
       }
       // FP32 transposing reduction of the 20 (sum, -compensation) pairs; only
       // the final hi + lo of each is formed in FP64
@@ -544,73 +517,62 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
     __syncthreads();
   }
 
-  // ---- 4. row sweeps (negative-xi rows first: warp-uniform direction), and
-  //         5. the store: as soon as a warp has swept its 32 rows of a round it
-  //         writes them out (with the f_n term of stages 2 and 3), so the
-  //         stores of one warp overlap the sweeps of the others.  Cell c of
-  //         the tile is position 4 + c. ----
+  // ---- 4. row sweeps (negative-xi rows first: warp-uniform direction) ----
   const float inv_dz = float(g.inv_dz), dt = float(g.dt);
+  for (int ir = tid; ir < V; ir += kNT) {
+    const int v = rowv[ir];
+    const float xi = tb.xi[v];
+    const int k = tb.kidx[v];
+    float2 wp2[kMP];
+#pragma unroll
+    for (int m = 0; m < kMP; ++m) wp2[m] = splat((m < g.nm) ? tb.wp[m * V + v] : 0.f);
+    const float* ck = coef + (size_t)k * kH * kMP * 2;
+    if (ir >= nneg) sweep_row2<true>(tile + v * kP, xi, wp2, g.nm, ck, gco, inv_dz, dt);
+    else sweep_row2<false>(tile + v * kP, xi, wp2, g.nm, ck, gco, inv_dz, dt);
+  }
+  __syncthreads();
+
+  // ---- 5. store: cell c of the tile is position 4 + c ----
   const float a = (stage == 1) ? 0.75f : 1.f / 3.f;
   const float b = (stage == 1) ? 0.25f : 2.f / 3.f;
-  const bool full = s0 + kB2 <= g.Z;
-  for (int r0 = 0; r0 < V; r0 += kNT) {
-    const int ir = r0 + tid;
-    if (ir < V) {
-      const int v = rowv[ir];
-      const float xi = tb.xi[v];
-      const int k = tb.kidx[v];
-      float2 wp2[kMP];
+  if (s0 + kB2 <= g.Z) {
+    // full tile: kB2/4 chunks of 4 cells per row, 16-byte accesses, eight loads
+    // of f_n in flight per thread
+    for (int base_i = tid; base_i < V * (kB2 / 4); base_i += kInflight * kNT) {
+      float4 fo[kInflight];
 #pragma unroll
-      for (int m = 0; m < kMP; ++m) wp2[m] = splat((m < g.nm) ? tb.wp[m * V + v] : 0.f);
-      const float* ck = coef + (size_t)k * kH * kMP * 2;
-      if (ir >= nneg) sweep_row2<true>(tile + v * kP, xi, wp2, g.nm, ck, gco, inv_dz, dt);
-      else sweep_row2<false>(tile + v * kP, xi, wp2, g.nm, ck, gco, inv_dz, dt);
-    }
-    __syncwarp();
-    const int w0 = r0 + 32 * warp;  // first row (in sweep order) of this warp
-    const int nr = min(32, V - w0);
-    if (nr <= 0) continue;
-    const int myv = (lane < nr) ? rowv[w0 + lane] : 0;
-    if (full) {
-      // kQ 16-byte chunks per row; item i = lane + 32 j is chunk i % kQ of
-      // the warp's row i / kQ; all f_n loads of a lane are in flight together
-      constexpr int kQ = kB2 / 4;
-      float4 fo[kQ];
-      int vo[kQ];
-#pragma unroll
-      for (int j = 0; j < kQ; ++j) {
-        const int i = lane + 32 * j;
-        const int r = i / kQ, q = i - r * kQ;
-        vo[j] = __shfl_sync(0xffffffffu, myv, r);
-        if (stage != 0 && r < nr)
-          fo[j] = __ldg(reinterpret_cast<const float4*>(fn + (size_t)vo[j] * g.ldz + s0 + 4 * q));
+      for (int u = 0; u < kInflight; ++u) {
+        const int idx = base_i + u * kNT;
+        if (stage != 0 && idx < V * (kB2 / 4)) {
+          const int v = idx / (kB2 / 4), q = idx - v * (kB2 / 4);
+          fo[u] = __ldg(reinterpret_cast<const float4*>(fn + (size_t)v * g.ldz + s0 + 4 * q));
+        }
       }
 #pragma unroll
-      for (int j = 0; j < kQ; ++j) {
-        const int i = lane + 32 * j;
-        const int r = i / kQ, q = i - r * kQ;
-        if (r < nr) {
-          float4 x = *reinterpret_cast<const float4*>(tile + vo[j] * kP + 4 + 4 * q);
+      for (int u = 0; u < kInflight; ++u) {
+        const int idx = base_i + u * kNT;
+        if (idx < V * (kB2 / 4)) {
+          const int v = idx / (kB2 / 4), q = idx - v * (kB2 / 4);
+          float4 r = *reinterpret_cast<const float4*>(tile + v * kP + 4 + 4 * q);
           if (stage != 0) {
-            x.x = a * fo[j].x + b * x.x;
-            x.y = a * fo[j].y + b * x.y;
-            x.z = a * fo[j].z + b * x.z;
-            x.w = a * fo[j].w + b * x.w;
+            r.x = a * fo[u].x + b * r.x;
+            r.y = a * fo[u].y + b * r.y;
+            r.z = a * fo[u].z + b * r.z;
+            r.w = a * fo[u].w + b * r.w;
           }
-          *reinterpret_cast<float4*>(fout + (size_t)vo[j] * g.ldz + s0 + 4 * q) = x;
+          *reinterpret_cast<float4*>(fout + (size_t)v * g.ldz + s0 + 4 * q) = r;
         }
       }
-    } else {
-      for (int i = lane; i < nr * kB2; i += 32) {
-        const int r = i / kB2, c = i - r * kB2;
-        const int sc = s0 + c;
-        if (sc < g.Z) {
-          const int v = rowv[w0 + r];
-          const size_t o = (size_t)v * g.ldz + sc;
-          float x = tile[v * kP + 4 + c];
-          if (stage != 0) x = a * fn[o] + b * x;
-          fout[o] = x;
-        }
+    }
+  } else {
+    for (int idx = tid; idx < V * kB2; idx += kNT) {
+      const int v = idx / kB2, c = idx - v * kB2;
+      const int sc = s0 + c;
+      if (sc < g.Z) {
+        const size_t o = (size_t)v * g.ldz + sc;
+        float r = tile[v * kP + 4 + c];
+        if (stage != 0) r = a * fn[o] + b * r;
+        fout[o] = r;
       }
     }
   }
@@ -711,7 +673,6 @@ bool sod32_make_maps(void* out4, const float* F0, const float* F1, const float* 
   if (Z < kB2 + 8 || (ldz % 4) != 0) return false;
   int nbox = 0;
   const int br = tma_box_rows(V, &nbox);
-  if (nbox > kMaxBoxes) return false;
   CUtensorMap* m = static_cast<CUtensorMap*>(out4);
   return make_map(&m[0], F0, Z, ldz, V, kC, br) && make_map(&m[1], F1, Z, ldz, V, kC, br) &&
          make_map(&m[2], F2, Z, ldz, V, kC, br) && make_map(&m[3], F0, Z, ldz, V, kB2, br);
@@ -741,8 +702,7 @@ cudaError_t sod32_stage_launch(const SodGeom& g, const SodTables<float>& tb, con
   std::memset(&mn, 0, sizeof(mn));
   // TMA needs 16-byte aligned bases and row stride (cudaMalloc'd buffers,
   // ldz a multiple of 32) and at least one whole interior tile
-  const bool tma = g.Z >= kB2 + 8 && nbox <= kMaxBoxes &&
-                   (reinterpret_cast<uintptr_t>(fin) % 16) == 0 &&
+  const bool tma = g.Z >= kB2 + 8 && (reinterpret_cast<uintptr_t>(fin) % 16) == 0 &&
                    (reinterpret_cast<uintptr_t>(fn) % 16) == 0 && (g.ldz % 4) == 0 &&
                    make_map(&m, fin, g.Z, g.ldz, g.V, kC, br) &&
                    make_map(&mn, fn, g.Z, g.ldz, g.V, kB2, br);
