@@ -530,7 +530,7 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
   long long img_total = 0;
   for (size_t i = 0; i < qvals.size(); ++i) {
     img_off[i] = img_total;
-    img_total += (long long)qvals[i] * ((qvals[i] + 31) / 32) * 32;
+    img_total += (long long)qvals[i] * ((qvals[i] + 31) / 32) * 64;  // hi and lo tiles
   }
   if (o->kp_mode == RSLB_KP_TF32X3) {
     const int rmax = std::max(1, kTcMaxCols / QL);

@@ -12,13 +12,14 @@
 // and the TF32 truncation of the lo parts leave ~2^-20 relative error per
 // product, FP32-level for this contraction.
 //
-// Data movement: K^P is stored once per distinct Q as an FP32 image whose
-// 128-row x 32-column tiles are already in the 128-byte-swizzled K-major
-// order the MMA descriptors expect; a tile is brought in by one bulk copy
-// (cp.async.bulk, completion on an mbarrier) and split into hi/lo in place.
-// The state f of the block is read from HBM/L2 per 32-row K-block, split and
-// stored swizzled by the threads.  Two pipeline stages: the bulk copy of
-// K-block it+1 and the thread work of K-block it+1 overlap the MMAs of it.
+// Data movement: K^P is stored once per distinct Q, already split: for every
+// 128-row x 32-column tile the image holds the hi part and then the lo part,
+// each in the 128-byte-swizzled K-major order the MMA descriptors expect; the
+// two are brought in by bulk copies (cp.async.bulk, completion on one
+// mbarrier) and used as they land.  The state f of the block is read from
+// HBM/L2 per 32-row K-block, split and stored swizzled by the threads.  Two
+// pipeline stages: the bulk copies of K-block it+1 and the thread work of
+// K-block it+1 overlap the MMAs of it.
 // The epilogue reads its row of D from TMEM (tcgen05.ld), adds the K^L and
 // -f/tau terms and the Anderson-Witting collision with the equilibrium of
 // the stage state, applies the RK combination and writes f and the run's
@@ -232,8 +233,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const float* Asrc = a.kimg + blk.img + (size_t)mt * 128 * nkb * 32;
+  // tile (mt, kb): hi at Asrc + kb * rows * 64, lo rows * 32 floats after it
+  const float* Asrc = a.kimg + blk.img + (size_t)mt * 128 * nkb * 64;
   const uint32_t abytes = (uint32_t)rows * 128u;
+  auto copy_a = [&](int s, int it) {
+    const float* src = Asrc + (size_t)it * rows * 64;
+    mbar_expect_tx(&full[s], 2 * abytes);
+    bulk_g2s(Ahi(s), src, abytes, &full[s]);
+    bulk_g2s(Alo(s), src + (size_t)rows * 32, abytes, &full[s]);
+  };
   const uint32_t idesc = idesc_tf32(NC);
   // The issuer (lane 0 of warp 4) keeps the bulk copies two K-blocks ahead
   // and issues the MMAs; issued-but-unconfirmed work is tracked for the
@@ -242,8 +250,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
   int last_copy = -1, last_commit = -1;
   if (issuer) {
     for (int it = 0; it < 2 && it < nkb; ++it) {
-      mbar_expect_tx(&full[it], abytes);
-      bulk_g2s(Ahi(it), Asrc + (size_t)it * rows * 32, abytes, &full[it]);
+      copy_a(it, it);
       last_copy = it;
     }
   }
@@ -287,17 +294,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
 
   // ---- main loop over K-blocks of 32 rows j' ----
   // Workers (warps 0-3): store the state rows of K-block it (loaded into
-  // registers during it-1) split into hi/lo, load those of it+1, split the
-  // landed K^P tile in place and arrive on ready[s].  Issuer: wait ready[s],
-  // issue the 12 MMAs, commit to done[s]; once they are done, refill stage s
-  // with the K^P tile of it+2.  No CTA-wide barrier inside the loop.
+  // registers during it-1) split into hi/lo, load those of it+1 and arrive
+  // on ready[s].  Issuer: wait full[s] (the K^P tiles) and ready[s], issue
+  // the 12 MMAs, commit to done[s]; once they are done, refill stage s with
+  // the K^P tiles of it+2.  No CTA-wide barrier inside the loop.
   const float* Fblk = a.Fin + blk.soff;
   int lost = 0;
   if (issuer) {
     for (int it = 0; it < nkb; ++it) {
       const int s = it & 1;
       const uint32_t par = (uint32_t)(it >> 1) & 1u;
-      if (!mbar_wait(&ready[s], par)) {
+      if (!mbar_wait(&full[s], par) || !mbar_wait(&ready[s], par)) {
         lost = 1;
         break;
       }
@@ -317,8 +324,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
           lost = 1;
           break;
         }
-        mbar_expect_tx(&full[s], abytes);
-        bulk_g2s(Ahi(s), Asrc + (size_t)(it + 2) * rows * 32, abytes, &full[s]);
+        copy_a(s, it + 2);
         last_copy = it + 2;
       }
     }
@@ -352,18 +358,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
         }
       }
       if (it + 1 < nkb) load_b(it + 1);
-      if (!mbar_wait(&full[s], par)) {
-        lost = 1;
-        break;
-      }
-      float4* ah = reinterpret_cast<float4*>(Ahi(s));
-      float4* al = reinterpret_cast<float4*>(Alo(s));
-      for (int i = tid; i < rows * 8; i += kTcWorkers) {
-        const float4 x = ah[i];
-        const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
-        ah[i] = h;
-        al[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-      }
       fence_proxy_async();
       mbar_arrive(&ready[s]);
     }
@@ -492,10 +486,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
   }
 }
 
-// K^P image of one Q: tile (mt, kb) = rows j in M-tile mt (rows(mt) of them)
-// x columns j' = 32 kb .. 32 kb + 31, swizzled, stored at
-// img + (mt * 128 * nkb + kb * rows(mt)) * 32 floats.  Columns j' >= Q stay
-// zero (the buffer is cleared first).
+// K^P image of one Q, split for 3xTF32: tile (mt, kb) = rows j in M-tile mt
+// (rows(mt) of them) x columns j' = 32 kb .. 32 kb + 31; its hi part
+// tf32(K) (round to nearest) is stored swizzled at
+// img + (mt * 128 * nkb + kb * rows(mt)) * 64 floats and its lo part K - hi
+// (exact in FP32) rows(mt) * 32 floats after it.  Columns j' >= Q stay zero
+// (the buffer is cleared first).
 __global__ void bj_tc_image_kernel(int Q, const double* __restrict__ xw, float* img) {
   const int nkb = (Q + 31) / 32;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -503,8 +499,11 @@ __global__ void bj_tc_image_kernel(int Q, const double* __restrict__ xw, float* 
   const int j = idx / Q, jp = idx - j * Q;
   const int mt = j >> 7, row = j & 127, kb = jp >> 5, col = jp & 31;
   const int rows = min(128, Q - 128 * mt);
-  float* tile = img + ((size_t)mt * 128 * nkb + (size_t)kb * rows) * 32;
-  tile[swz(row, col) >> 2] = float(kp_entry(Q, xw, j, jp));
+  float* tile = img + ((size_t)mt * 128 * nkb + (size_t)kb * rows) * 64;
+  const float x = float(kp_entry(Q, xw, j, jp));
+  const float hi = tf32_rn(x);
+  tile[swz(row, col) >> 2] = hi;
+  tile[(size_t)rows * 32 + (swz(row, col) >> 2)] = x - hi;
 }
 
 // Moments (N, E) of each run into partial slot 0 (slots 1-3 cleared).
