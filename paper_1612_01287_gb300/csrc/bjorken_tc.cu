@@ -178,7 +178,7 @@ __device__ __forceinline__ void tc_report(int* err, int code, int run) {
 // The stage kernel
 // ---------------------------------------------------------------------------
 template <int QL>
-__global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   const BjTcBlock blk = a.blocks[blockIdx.x];
   const int Q = blk.Q, R = blk.R, NC = blk.nc, mt = blk.mt;
@@ -420,45 +420,61 @@ __global__ void __launch_bounds__(kTcThreads, 1) bj_tc_stage_kernel(BjTcArgs a) 
       for (int p = 0; p < QL; ++p)
         if (c0 + 16 * p < NC) tmem_ld16(trow + (uint32_t)(c0 + 16 * p), d + 16 * p);
       tmem_wait_ld();
+      // four runs at a time: all their loads of f^(i) and f_n are issued
+      // before any of their stores (the output may alias f_n, so the loads of
+      // a later run could not move above the stores of an earlier one)
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int r = rb + i;
-        float on = 0.f, oe = 0.f;
-        if (r < R && rowok) {
-          float fk[QL];
+      for (int g = 0; g < 16; g += 4) {
+        float fk[4][QL], fnv[4][QL];
 #pragma unroll
-          for (int k = 0; k < QL; ++k) fk[k] = Fin[(size_t)(r * QL + k) * Q + j];
-          if (!rk) {
+        for (int ii = 0; ii < 4; ++ii) {
+          const int r = rb + g + ii;
 #pragma unroll
-            for (int k = 0; k < QL; ++k)
-              a.dout[blk.soff + (size_t)(r * QL + k) * Q + j] = __uint_as_float(d[i * QL + k]);
-          } else {
-            const float rate = rs[r], neq4 = rs[R + r], omt = rs[2 * R + r];
-#pragma unroll
-            for (int k = 0; k < QL; ++k) {
-              float klf = 0.f;
-#pragma unroll
-              for (int q = 0; q < QL; ++q) klf += KL[k * QL + q] * fk[q];
-              const float feq = neq4 * (wj * wk[k]) * (1.f + l1[k] * omt);
-              const float L = (-fk[k] + xi2 * klf + __uint_as_float(d[i * QL + k])) * itau -
-                              (fk[k] - feq) * rate;
-              const float v = fk[k] + dt * L;
-              const size_t o = (size_t)(r * QL + k) * Q + j;
-              float out = v;
-              if (a.stage == 1) out = ca * Fn[o] + cb * v;
-              else if (a.stage == 2) out = Fn[o] * ca + cb * v;
-              Fout[o] = out;
-              on += out;
-              oe += xk[k] * out;
-            }
+          for (int k = 0; k < QL; ++k) {
+            const size_t o = (size_t)(r * QL + k) * Q + j;
+            const bool ok = r < R && rowok;
+            fk[ii][k] = ok ? Fin[o] : 0.f;
+            fnv[ii][k] = (ok && rk && a.stage != 0) ? Fn[o] : 0.f;
           }
         }
-        if (rk) {
-          on = warp_sum_f(on);
-          oe = warp_sum_f(oe);
-          if (lane == 0 && r < R) {
-            mp[(warp * R + r) * 2] = on;
-            mp[(warp * R + r) * 2 + 1] = oe;
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) {
+          const int i = g + ii, r = rb + i;
+          float on = 0.f, oe = 0.f;
+          if (r < R && rowok) {
+            if (!rk) {
+#pragma unroll
+              for (int k = 0; k < QL; ++k)
+                a.dout[blk.soff + (size_t)(r * QL + k) * Q + j] = __uint_as_float(d[i * QL + k]);
+            } else {
+              const float rate = rs[r], neq4 = rs[R + r], omt = rs[2 * R + r];
+#pragma unroll
+              for (int k = 0; k < QL; ++k) {
+                float klf = 0.f;
+#pragma unroll
+                for (int q = 0; q < QL; ++q) klf += KL[k * QL + q] * fk[ii][q];
+                const float feq = neq4 * (wj * wk[k]) * (1.f + l1[k] * omt);
+                const float L =
+                    (-fk[ii][k] + xi2 * klf + __uint_as_float(d[i * QL + k])) * itau -
+                    (fk[ii][k] - feq) * rate;
+                const float v = fk[ii][k] + dt * L;
+                const size_t o = (size_t)(r * QL + k) * Q + j;
+                float out = v;
+                if (a.stage == 1) out = ca * fnv[ii][k] + cb * v;
+                else if (a.stage == 2) out = fnv[ii][k] * ca + cb * v;
+                Fout[o] = out;
+                on += out;
+                oe += xk[k] * out;
+              }
+            }
+          }
+          if (rk) {
+            on = warp_sum_f(on);
+            oe = warp_sum_f(oe);
+            if (lane == 0 && r < R) {
+              mp[(warp * R + r) * 2] = on;
+              mp[(warp * R + r) * 2 + 1] = oe;
+            }
           }
         }
       }
