@@ -164,12 +164,6 @@ __host__ __device__ __forceinline__ uint32_t swz(int row, int col) {
   return (uint32_t)(row * 128 + ((((col >> 2) ^ row) & 7) << 4) + ((col & 3) << 2));
 }
 
-__device__ __forceinline__ float warp_sum_f(float x) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
-
 __device__ __forceinline__ void tc_report(int* err, int code, int run) {
   if (atomicCAS(err, 0, code) == 0) err[1] = run;
 }
@@ -203,13 +197,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   float* rs = reinterpret_cast<float*>(tail + 64);  // rate[R] | neq4[R] | omt[R]
   float* mp = rs + 3 * R;                           // [4 warps][R][2]
 
-  // zero the A buffers (rows past the end of K^P stay zero), set up barriers
+  // zero the rows of the A buffers that the copies do not fill (past the
+  // end of K^P in a partial M-tile), set up barriers
   {
-    float4* z = reinterpret_cast<float4*>(base);
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int s = 0; s < 2; ++s)
-      for (int i = tid; i < (int)(2 * kATile / 16); i += kTcThreads)
-        z[s * (sstride / 16) + i] = zero;
+      for (int h = 0; h < 2; ++h) {
+        float4* z = reinterpret_cast<float4*>(base + s * sstride + h * kATile);
+        for (int i = rows * 8 + tid; i < (int)(kATile / 16); i += kTcThreads) z[i] = zero;
+      }
   }
   if (tid == 0) {
     mbar_init(&full[0], 1);
@@ -341,7 +337,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
     load_b(0);
     for (int it = 0; it < nkb; ++it) {
       const int s = it & 1;
-      const uint32_t par = (uint32_t)(it >> 1) & 1u;
       // stage s was last read by the MMAs of it-2
       if (it >= 2 && !mbar_wait(&done[s], (uint32_t)((it - 2) >> 1) & 1u)) {
         lost = 1;
@@ -437,6 +432,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
             fnv[ii][k] = (ok && rk && a.stage != 0) ? Fn[o] : 0.f;
           }
         }
+        float mv[8];  // (N, E) partials of the four runs
 #pragma unroll
         for (int ii = 0; ii < 4; ++ii) {
           const int i = g + ii, r = rb + i;
@@ -468,14 +464,35 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
               }
             }
           }
-          if (rk) {
-            on = warp_sum_f(on);
-            oe = warp_sum_f(oe);
-            if (lane == 0 && r < R) {
-              mp[(warp * R + r) * 2] = on;
-              mp[(warp * R + r) * 2 + 1] = oe;
-            }
+          mv[2 * ii] = on;
+          mv[2 * ii + 1] = oe;
+        }
+        if (rk) {
+          // warp sums of the eight values by a transposing reduction: lanes
+          // with the level's bit set keep the upper half of their values and
+          // trade the lower half with the partner lane (9 shuffles, not 40)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const bool up = lane & 16;
+            const float send = up ? mv[i] : mv[i + 4], keep = up ? mv[i + 4] : mv[i];
+            mv[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
           }
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const bool up = lane & 8;
+            const float send = up ? mv[i] : mv[i + 2], keep = up ? mv[i + 2] : mv[i];
+            mv[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+          }
+          {
+            const bool up = lane & 4;
+            const float send = up ? mv[0] : mv[1], keep = up ? mv[1] : mv[0];
+            mv[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+          }
+          mv[0] += __shfl_xor_sync(0xffffffffu, mv[0], 2);
+          mv[0] += __shfl_xor_sync(0xffffffffu, mv[0], 1);
+          // lane 4 m (m < 8) holds value m = 2 (run) + (0: N, 1: E)
+          const int m = lane >> 2, r = rb + g + (m >> 1);
+          if ((lane & 3) == 0 && r < R) mp[(warp * R + r) * 2 + (m & 1)] = mv[0];
         }
       }
     }
