@@ -38,7 +38,8 @@ namespace {
 constexpr int kTcThreads = 160;  // 4 worker warps + 1 issuer warp
 constexpr int kTcWorkers = 128;
 constexpr uint32_t kATile = 128 * 128;  // bytes: 128 rows x 32 FP32
-constexpr int kSpinLimit = 1 << 22;
+constexpr int kSpinLimit = 150000;       // try_wait rounds of at most kSuspendNs: ~0.3 s
+constexpr uint32_t kSuspendNs = 2000;
 constexpr int kErrTimeout = 97;
 constexpr int kTcMaxRowsPerWarp = kTcMaxCols / 4;  // state rows per warp in a K-block
 
@@ -60,23 +61,24 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+// One potentially blocking test: the thread is suspended until the phase
+// completes or about kSuspendNs have passed, so a waiting warp does not take
+// issue slots from the others.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(su32(bar)), "r"(parity)
+      : "r"(su32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
 
 // Bounded wait for the phase of the given parity to complete.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < kSpinLimit; ++i) {
-    if (mbar_test(bar, parity)) return true;
-    if (i > 64) __nanosleep(64);
-  }
+  for (int i = 0; i < kSpinLimit; ++i)
+    if (mbar_try(bar, parity)) return true;
   return false;
 }
 
