@@ -253,10 +253,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
     }
   }
 
-  // per-run equilibrium of the stage state from the moment partials
+  // per-run equilibrium of the stage state from the moment partials, by the
+  // issuer's 31 idle lanes while the workers start on the K-loop (the
+  // epilogue reads it after the CTA barrier that ends the loop)
   const bool rk = a.stage >= 0;
-  if (rk) {
-    for (int r = tid; r < R; r += kTcThreads) {
+  if (rk && warp == 4 && lane > 0) {
+    for (int r = lane - 1; r < R; r += 31) {
       const int gr = blk.first + r;
       double N = 0.0, E = 0.0;
       for (int m = 0; m < blk.nmt; ++m) {
@@ -287,6 +289,28 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
       rs[r] = float(rate);
       rs[R + r] = float(neq4);
       rs[2 * R + r] = float(omt);
+    }
+  }
+
+  // what the epilogue needs from global memory, loaded before the K-loop so
+  // the latency is not paid after it: row j of D per worker thread
+  const int j = 128 * mt + 32 * (warp & 3) + lane;
+  const bool rowok = j < Q;
+  float xi2 = 0.f, wj = 0.f;
+  float KL[QL * QL], xk[QL], wk[QL], l1[QL];
+  if (warp < 4) {
+    if (rowok) {
+      const double x = a.npool[blk.xoff + j];
+      xi2 = float(x * x);
+      wj = float(a.npool[blk.xoff + Q + j]);
+    }
+#pragma unroll
+    for (int k = 0; k < QL; ++k) {
+      xk[k] = float(a.xk[k]);
+      wk[k] = float(a.wk[k]);
+      l1[k] = float(3.0 - a.xk[k]);
+#pragma unroll
+      for (int q = 0; q < QL; ++q) KL[k * QL + q] = float(a.KL[k * QL + q]);
     }
   }
 
@@ -387,23 +411,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
 
   // ---- epilogue (worker warps): row j of D per thread ----
   if (warp < 4) {
-    const int j = 128 * mt + 32 * warp + lane;
-    const bool rowok = j < Q;
-    float xi2 = 0.f, wj = 0.f;
-    if (rowok) {
-      const double x = a.npool[blk.xoff + j];
-      xi2 = float(x * x);
-      wj = float(a.npool[blk.xoff + Q + j]);
-    }
-    float KL[QL * QL], xk[QL], wk[QL], l1[QL];
-#pragma unroll
-    for (int k = 0; k < QL; ++k) {
-      xk[k] = float(a.xk[k]);
-      wk[k] = float(a.wk[k]);
-      l1[k] = float(3.0 - a.xk[k]);
-#pragma unroll
-      for (int q = 0; q < QL; ++q) KL[k * QL + q] = float(a.KL[k * QL + q]);
-    }
     const float itau = float(1.0 / a.tau), dt = float(a.dtau);
     const float ca = a.stage == 1 ? 0.75f : 1.f / 3.f, cb = a.stage == 1 ? 0.25f : 2.f / 3.f;
     const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
