@@ -75,8 +75,11 @@ __device__ __forceinline__ float2 weno_corr2(float2 D0, float2 D1, float2 D2, fl
   // instead of a reciprocal
   const float mx = fmaxf(s1.x, fmaxf(s2.x, s3.x));
   const float my = fmaxf(s1.y, fmaxf(s2.y, s3.y));
+  // 2^(127 - e) for the biased exponent e of m: an AND and a subtract; a
+  // zero or subnormal m gives 2^127, which keeps zero sigmas zero and brings
+  // subnormal ones into range
   auto inv_pow2 = [&](float m) {
-    return m > tiny ? __int_as_float((254 - ((__float_as_int(m) >> 23) & 0xff)) << 23) : 0.f;
+    return __int_as_float(0x7F000000 - (__float_as_int(m) & 0x7F800000));
   };
   const float2 inv = make_float2(inv_pow2(mx), inv_pow2(my));
   const float2 r1 = mul2(s1, inv), r2 = mul2(s2, inv), r3 = mul2(s3, inv);
