@@ -151,22 +151,22 @@ __device__ __forceinline__ T weno_corr(T D0, T D1, T D2, T D3, T K1, T K2, T K3)
   const T s2 = K2 + T(0.25) * e2 * e2;
   const T s3 = K3 + T(0.25) * e3 * e3;
   const T g1 = T(5) * D1 - T(2) * D0, g2 = D1 + T(2) * D2, g3 = T(4) * D2 - D3;
-  // Values below the smallest normal number count as zero: the FP32 reciprocal
-  // flushes subnormal inputs, and a vanishing denominator means the
-  // correction vanishes (limit rules).
+  // A denominator below the smallest normal number counts as zero: the FP32
+  // reciprocal flushes subnormal inputs, and a vanishing denominator means
+  // the correction vanishes (limit rules).
   // The indicators are scaled by the power of two at or below their maximum
   // (the weights are homogeneous in sigma; the scaling only keeps the fourth
-  // powers in range), formed from the exponent bits instead of a reciprocal.
+  // powers in range), formed from the exponent bits with an AND and a
+  // subtract; a zero or subnormal maximum gives the largest such power, which
+  // keeps zero indicators zero and brings subnormal ones into range.
   const T tiny = Prec<T>::tiny();
   const T smax = fmax(s1, fmax(s2, s3));
-  T inv = T(0);
-  if (smax > tiny) {
-    if constexpr (sizeof(T) == 4)
-      inv = __int_as_float((254 - ((__float_as_int(smax) >> 23) & 0xff)) << 23);
-    else
-      inv = __longlong_as_double((long long)(2046 - ((__double_as_longlong(smax) >> 52) & 0x7ff))
-                                 << 52);
-  }
+  T inv;
+  if constexpr (sizeof(T) == 4)
+    inv = __int_as_float(0x7F000000 - (__float_as_int(smax) & 0x7F800000));
+  else
+    inv = __longlong_as_double(0x7FE0000000000000LL -
+                               (__double_as_longlong(smax) & 0x7FF0000000000000LL));
   const T r1 = s1 * inv, r2 = s2 * inv, r3 = s3 * inv;
   const T t1 = r1 * r1, t2 = r2 * r2, t3 = r3 * r3;
   const T n1 = T(0.1) * (t2 * t3), n2 = T(0.6) * (t1 * t3), n3 = T(0.3) * (t1 * t2);
