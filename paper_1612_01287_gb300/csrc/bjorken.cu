@@ -73,11 +73,12 @@ __device__ __forceinline__ void bj_report(int* err, int code, int run) {
 // Output transposed: KT[j'][j].
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void bj_kp_kernel(int Q, const double* __restrict__ xw, T* KT) {
+__global__ void bj_kp_kernel(int Q, const double* __restrict__ xw, const double* __restrict__ kc,
+                             T* KT) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= Q * Q) return;
   const int j = idx / Q, jp = idx - j * Q;
-  KT[(size_t)jp * Q + j] = T(kp_entry(Q, xw, j, jp));
+  KT[(size_t)jp * Q + j] = T(kp_entry(Q, xw, kc, j, jp));
 }
 
 // K^L of Eq. K_lag_disc (Q_L x Q_L), FP64, one thread per entry.
@@ -334,6 +335,7 @@ struct rslb_bjorken {
   void* state;
   void* kpool;
   double* npool;
+  double* kpc;  // kp_coefficients up to the largest Q
   BjBlock* blocks;
   BjQTab* qtab;
   long long* roff;
@@ -363,7 +365,7 @@ namespace {
 
 void bj_free(rslb_bjorken* b) {
   if (!b) return;
-  void* ptrs[] = {b->state, b->kpool, b->npool, b->blocks, b->qtab, b->roff, b->xoff, b->rq,
+  void* ptrs[] = {b->state, b->kpool, b->npool, b->kpc, b->blocks, b->qtab, b->roff, b->xoff, b->rq,
                   b->tau_aw0, b->gas, b->user, b->xk, b->wk, b->KL, b->err, b->out_dev,
                   b->tcblocks, b->kimg, b->F1, b->F2, b->mp[0], b->mp[1], b->ytmp};
   for (void* p : ptrs)
@@ -574,6 +576,12 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
 
   int rc = RSLB_OK;
   if (!rc) rc = dev_upload(&b->npool, npool.data(), npool.size());
+  if (!rc) {
+    const int qmax = *std::max_element(qvals.begin(), qvals.end());
+    std::vector<double> kc((size_t)kKpCoef * qmax);
+    kp_coefficients(qmax, kc.data());
+    rc = dev_upload(&b->kpc, kc.data(), kc.size());
+  }
   if (!rc) rc = dev_upload(&b->qtab, qtab.data(), qtab.size());
   if (!rc) rc = dev_upload(&b->blocks, blocks.data(), blocks.size());
   if (!rc) rc = dev_upload(&b->roff, roff.data(), roff.size());
@@ -619,15 +627,15 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
     const int n = Q * Q;
     if (b->precision == RSLB_F64)
       bj_kp_kernel<double><<<(n + 255) / 256, 256, 0, st>>>(
-          Q, b->npool + qtab[i].xi_off, (double*)b->kpool + qtab[i].kp_off);
+          Q, b->npool + qtab[i].xi_off, b->kpc, (double*)b->kpool + qtab[i].kp_off);
     else
       bj_kp_kernel<float><<<(n + 255) / 256, 256, 0, st>>>(
-          Q, b->npool + qtab[i].xi_off, (float*)b->kpool + qtab[i].kp_off);
+          Q, b->npool + qtab[i].xi_off, b->kpc, (float*)b->kpool + qtab[i].kp_off);
   }
   if (o->kp_mode == RSLB_KP_TF32X3) {
     cudaMemsetAsync(b->kimg, 0, sizeof(float) * (size_t)img_total, st);
     for (size_t i = 0; i < qvals.size(); ++i)
-      bj_tc_image_launch(qvals[i], b->npool + qtab[i].xi_off, b->kimg + img_off[i], st);
+      bj_tc_image_launch(qvals[i], b->npool + qtab[i].xi_off, b->kpc, b->kimg + img_off[i], st);
   }
   bj_kl_kernel<<<1, QL * QL, 0, st>>>(QL, b->xk, b->wk, b->KL);
   if (b->precision == RSLB_F64)

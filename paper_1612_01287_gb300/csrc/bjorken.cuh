@@ -10,8 +10,29 @@ namespace rslb {
 //                ((2m-1)(2m+3)) + (m-1)/(2m-1) P_{m-2}(xi_j') ]
 // xw = [xi_0 .. xi_{Q-1} | w_0 .. w_{Q-1}].  P_m(xi_j) advances by the
 // Bonnet recurrence; the xi_j' values are carried as a window
-// P_{m-2} .. P_{m+2}.
-__device__ inline double kp_entry(int Q, const double* __restrict__ xw, int j, int jp) {
+// P_{m-2} .. P_{m+2}.  kc holds, per m, the m-dependent factors of both sums
+// and of both recurrences (kp_coefficients), so the loop has no divisions.
+constexpr int kKpCoef = 8;
+
+// Host: kc[m * kKpCoef + i] for m = 0 .. qmax - 1.
+inline void kp_coefficients(int qmax, double* kc) {
+  for (int m = 0; m < qmax; ++m) {
+    const double d = m;
+    double* c = kc + (size_t)m * kKpCoef;
+    c[0] = d * (d + 1.0) * (d + 2.0) / (2.0 * (2.0 * d + 3.0));
+    c[1] = m >= 1 ? 0.5 * d * (d + 1.0) * (2.0 * d + 1.0) / ((2.0 * d - 1.0) * (2.0 * d + 3.0))
+                  : 0.0;
+    c[2] = m >= 1 ? 0.5 * d * (d + 1.0) * (d - 1.0) / (2.0 * d - 1.0) : 0.0;
+    c[3] = (2.0 * d + 1.0) / (d + 1.0);  // P_{m+1} = c3 x P_m - c4 P_{m-1}
+    c[4] = d / (d + 1.0);
+    c[5] = (2.0 * d + 5.0) / (d + 3.0);  // P_{m+3} = c5 y P_{m+2} - c6 P_{m+1}
+    c[6] = (d + 2.0) / (d + 3.0);
+    c[7] = 0.0;
+  }
+}
+
+__device__ inline double kp_entry(int Q, const double* __restrict__ xw,
+                                  const double* __restrict__ kc, int j, int jp) {
   const double x = xw[j], y = xw[jp], w = xw[Q + j];
   double px = x, pxm1 = 1.0;  // P_1(x), P_0(x)
   double ym2 = 0.0, ym1 = 1.0, y0 = y;
@@ -19,15 +40,17 @@ __device__ inline double kp_entry(int Q, const double* __restrict__ xw, int j, i
   double yp2 = (5.0 * y * yp1 - 2.0 * y0) / 3.0;
   double s1 = 0.0, s2 = 0.0;
   for (int m = 1; m <= Q - 1; ++m) {
-    const double dm = m;
-    if (m <= Q - 3) s1 += dm * (dm + 1.0) * (dm + 2.0) / (2.0 * (2.0 * dm + 3.0)) * px * yp2;
-    s2 += 0.5 * dm * (dm + 1.0) * px *
-          ((2.0 * dm + 1.0) / ((2.0 * dm - 1.0) * (2.0 * dm + 3.0)) * y0 +
-           (dm - 1.0) / (2.0 * dm - 1.0) * ym2);
-    const double pxn = ((2.0 * dm + 1.0) * x * px - dm * pxm1) / (dm + 1.0);
+    const double* c = kc + (size_t)m * kKpCoef;
+    const double2 c01 = *reinterpret_cast<const double2*>(c);
+    const double2 c23 = *reinterpret_cast<const double2*>(c + 2);
+    const double2 c45 = *reinterpret_cast<const double2*>(c + 4);
+    const double c6 = c[6];
+    if (m <= Q - 3) s1 += c01.x * px * yp2;
+    s2 += px * (c01.y * y0 + c23.x * ym2);
+    const double pxn = c23.y * x * px - c45.x * pxm1;
     pxm1 = px;
     px = pxn;
-    const double yn = ((2.0 * dm + 5.0) * y * yp2 - (dm + 2.0) * yp1) / (dm + 3.0);
+    const double yn = c45.y * y * yp2 - c6 * yp1;
     ym2 = ym1;
     ym1 = y0;
     y0 = yp1;
@@ -78,7 +101,8 @@ constexpr int kTcMaxCols = 80;
 cudaError_t bj_tc_set_attributes();
 size_t bj_tc_smem_bytes(int nc, int R);
 cudaError_t bj_tc_stage_launch(const BjTcArgs& a, int nblocks, size_t smem, cudaStream_t st);
-cudaError_t bj_tc_image_launch(int Q, const double* xw, float* img, cudaStream_t st);
+cudaError_t bj_tc_image_launch(int Q, const double* xw, const double* kc, float* img,
+                               cudaStream_t st);
 cudaError_t bj_tc_moments_launch(int nruns, int QL, const int* rq, const long long* roff,
                                  const double* xk, const float* state, double* mp,
                                  cudaStream_t st);

@@ -534,7 +534,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
 // img + (mt * 128 * nkb + kb * rows(mt)) * 64 floats and its lo part K - hi
 // (exact in FP32) rows(mt) * 32 floats after it.  Columns j' >= Q stay zero
 // (the buffer is cleared first).
-__global__ void bj_tc_image_kernel(int Q, const double* __restrict__ xw, float* img) {
+__global__ void bj_tc_image_kernel(int Q, const double* __restrict__ xw,
+                                   const double* __restrict__ kc, float* img) {
   const int nkb = (Q + 31) / 32;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= Q * Q) return;
@@ -542,7 +543,7 @@ __global__ void bj_tc_image_kernel(int Q, const double* __restrict__ xw, float* 
   const int mt = j >> 7, row = j & 127, kb = jp >> 5, col = jp & 31;
   const int rows = min(128, Q - 128 * mt);
   float* tile = img + ((size_t)mt * 128 * nkb + (size_t)kb * rows) * 64;
-  const float x = float(kp_entry(Q, xw, j, jp));
+  const float x = float(kp_entry(Q, xw, kc, j, jp));
   const float hi = tf32_rn(x);
   tile[swz(row, col) >> 2] = hi;
   tile[(size_t)rows * 32 + (swz(row, col) >> 2)] = x - hi;
@@ -598,9 +599,10 @@ cudaError_t bj_tc_stage_launch(const BjTcArgs& a, int nblocks, size_t smem, cuda
   return cudaGetLastError();
 }
 
-cudaError_t bj_tc_image_launch(int Q, const double* xw, float* img, cudaStream_t st) {
+cudaError_t bj_tc_image_launch(int Q, const double* xw, const double* kc, float* img,
+                               cudaStream_t st) {
   const int n = Q * Q;
-  bj_tc_image_kernel<<<(n + 255) / 256, 256, 0, st>>>(Q, xw, img);
+  bj_tc_image_kernel<<<(n + 255) / 256, 256, 0, st>>>(Q, xw, kc, img);
   return cudaGetLastError();
 }
 
