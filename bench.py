@@ -198,6 +198,16 @@ HBARC_GEV_FM = 0.1973269804
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
+def measured_tf32_peak():
+    """Dense TF32 tensor peak: the measured BF16 GEMM burst rate times the nominal
+    TF32/BF16 ratio 1/2 (1.1 vs 2.25 PFLOP/s); None without the measurement."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["bf16_tflops"]) / 2.0
+    except Exception:
+        return None
+
+
 def _timed(stream, fn, n):
     import torch
     torch.cuda.synchronize()
@@ -232,6 +242,15 @@ def bench_bjorken(stream, steps=None):
         out[mode] = {"value": cv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                      "steps": steps, "kp_tflops": flops / (ms * 1e-3) / 1e12,
                      "fp32_peak_tflops": FP32_PEAK_TFLOPS}
+        if mode == "tf32x3":
+            # the contraction as a tensor-core roofline: three TF32 products per
+            # FP32 product (hi.hi, hi.lo, lo.hi) against the dense TF32 peak
+            peak = measured_tf32_peak()
+            pipe = 3 * flops / (ms * 1e-3) / 1e12
+            out[mode]["tensor_roofline"] = {
+                "bound": "tensor", "achieved": pipe, "unit": "TFLOP/s",
+                "peak": peak, "frac": pipe / peak if peak else None,
+                "peak_source": "measured bf16 x 1/2" if peak else None}
     return out
 
 

@@ -371,41 +371,50 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
     // ---- 2. moments: warp w owns cells 4w .. 4w+3 of the tile, lanes own rows;
     //         blocks of four rows, Kahan-compensated across blocks ----
     {
-      float s[4][5], cpen[4][5];
+      // cells (0, 1) and (2, 3) of the warp's four are the two lanes of packed
+      // FP32x2 values (adjacent in the 16-byte loads): same roundings as the
+      // scalar fma / Kahan steps, half the instructions
+      float2 s2[2][5], c2[2][5];
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+      for (int p = 0; p < 2; ++p)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) { s[c][q] = 0.f; cpen[c][q] = 0.f; }
+        for (int q = 0; q < 5; ++q) { s2[p][q] = splat(0.f); c2[p][q] = splat(0.f); }
       for (int v0 = lane; v0 < V; v0 += 128) {
-        float blk[4][5];
+        float2 b2[2][5];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
+        for (int p = 0; p < 2; ++p)
 #pragma unroll
-          for (int q = 0; q < 5; ++q) blk[c][q] = 0.f;
+          for (int q = 0; q < 5; ++q) b2[p][q] = splat(0.f);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int v = v0 + 32 * u;
           if (v < V) {
             const float4 x = *reinterpret_cast<const float4*>(tile + v * kP + 4 + 4 * warp);
-            const float e[4] = {x.x, x.y, x.z, x.w};
-            float w[5];
+            const float2 X0 = make_float2(x.x, x.y), X1 = make_float2(x.z, x.w);
 #pragma unroll
-            for (int q = 0; q < 5; ++q) w[q] = mws[q * V + v];
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-#pragma unroll
-              for (int q = 0; q < 5; ++q) blk[c][q] = fmaf(e[c], w[q], blk[c][q]);
+            for (int q = 0; q < 5; ++q) {
+              const float2 W = splat(mws[q * V + v]);
+              b2[0][q] = fma2(X0, W, b2[0][q]);
+              b2[1][q] = fma2(X1, W, b2[1][q]);
+            }
           }
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
+        for (int p = 0; p < 2; ++p)
 #pragma unroll
           for (int q = 0; q < 5; ++q) {
-            const float y = blk[c][q] - cpen[c][q];
-            const float t = s[c][q] + y;
-            cpen[c][q] = (t - s[c][q]) - y;
-            s[c][q] = t;
+            const float2 y = sub2(b2[p][q], c2[p][q]);
+            const float2 t = add2(s2[p][q], y);
+            c2[p][q] = sub2(sub2(t, s2[p][q]), y);
+            s2[p][q] = t;
           }
+      }
+      float s[4][5], cpen[4][5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        s[0][q] = s2[0][q].x; s[1][q] = s2[0][q].y; s[2][q] = s2[1][q].x; s[3][q] = s2[1][q].y;
+        cpen[0][q] = c2[0][q].x; cpen[1][q] = c2[0][q].y;
+        cpen[2][q] = c2[1][q].x; cpen[3][q] = c2[1][q].y;
       }
       // FP32 transposing reduction of the 20 (sum, -compensation) pairs; only
       // the final hi + lo of each is formed in FP64
