@@ -326,10 +326,11 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
   if (c.bc == RSLB_BC_PERIODIC && c.Z < 6)
     return set_error(RSLB_ERR_ARG, "rslb_init: periodic domains need Z >= 6");
   const int Qx = c.Q_xi, QL = c.Q_L, V = Qx * QL, nm = c.N_Omega + 1;
-  std::vector<double> xj(Qx), wj(Qx), xk(QL), wk(QL), glt(kAeqNodes), glw(kAeqNodes);
+  std::vector<double> xj(Qx), wj(Qx), xk(QL), wk(QL), glt(kAeqTable), glw(kAeqTable);
   gauss_legendre_host(Qx, xj.data(), wj.data());
   gauss_laguerre2_host(QL, xk.data(), wk.data());
   gauss_legendre_host(kAeqNodes, glt.data(), glw.data());
+  gauss_legendre_host(kAeqNodesF32, glt.data() + kAeqNodes, glw.data() + kAeqNodes);
   const double dz = (c.z_max - c.z_min) / c.Z;
   double ximax = 0.0;
   for (double v : xj) ximax = std::fmax(ximax, std::fabs(v));

@@ -117,7 +117,7 @@ static int noalloc_run(const rslb_config& c, void* f, int nsteps, cudaStream_t s
   const size_t omw = take(es * 5 * V), oxi = take(es * V), owp = take(es * kMaxM * V),
                oL1 = take(es * kNoAllocMaxQL), ogL = take(es * V), ogR = take(es * V),
                okidx = take(sizeof(int) * V), orow = take(sizeof(int) * V),
-               oglt = take(sizeof(double) * kAeqNodes), oglw = take(sizeof(double) * kAeqNodes),
+               oglt = take(sizeof(double) * kAeqTable), oglw = take(sizeof(double) * kAeqTable),
                odxi = take(sizeof(double) * V), odp = take(sizeof(double) * V),
                odwp = take(sizeof(double) * kMaxM * V), odL1 = take(sizeof(double) * kNoAllocMaxQL),
                oq = take(sizeof(double) * (2 * Qx + 2 * QL)), odg = take(sizeof(double) * 6),
@@ -131,10 +131,11 @@ static int noalloc_run(const rslb_config& c, void* f, int nsteps, cudaStream_t s
 
   // quadrature on the host (stack arrays; V <= kNoAllocMaxV was checked)
   double q[2 * kNoAllocMaxV + 2 * kNoAllocMaxQL];
-  double glt[kAeqNodes], glw[kAeqNodes];
+  double glt[kAeqTable], glw[kAeqTable];
   gauss_legendre_host(Qx, q, q + Qx);
   gauss_laguerre2_host(QL, q + 2 * Qx, q + 2 * Qx + QL);
   gauss_legendre_host(kAeqNodes, glt, glw);
+  gauss_legendre_host(kAeqNodesF32, glt + kAeqNodes, glw + kAeqNodes);
   const double dz = (c.z_max - c.z_min) / c.Z;
   double ximax = 0.0;
   for (int j = 0; j < Qx; ++j) ximax = std::fmax(ximax, std::fabs(q[j]));

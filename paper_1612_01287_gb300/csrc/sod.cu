@@ -458,8 +458,11 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
         T J3[kMaxM], J4[kMaxM];
 #pragma unroll
         for (int m = 0; m < kMaxM; ++m) { J3[m] = T(0); J4[m] = T(0); }
-        for (int i = q; i < kAeqNodes; i += G)
-          aeq_node<T>(T(tb.gl_t[i]), T(tb.gl_w[i]), A, sh2, uinv, at_rest, g.nm, J3, J4);
+        // FP32 with N_Omega <= 7: the 16-node rule (stored after the 32-node one)
+        const bool short_rule = sizeof(T) == 4 && g.nm <= 8;
+        const int nn = short_rule ? kAeqNodesF32 : kAeqNodes, n0 = short_rule ? kAeqNodes : 0;
+        for (int i = q; i < nn; i += G)
+          aeq_node<T>(T(tb.gl_t[n0 + i]), T(tb.gl_w[n0 + i]), A, sh2, uinv, at_rest, g.nm, J3, J4);
 #pragma unroll
         for (int off = G / 2; off >= 1; off >>= 1)
 #pragma unroll

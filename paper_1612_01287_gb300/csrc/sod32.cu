@@ -481,7 +481,7 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
     }
     __syncthreads();
 
-    // ---- 3b. f^eq coefficients: 8 threads per cell share the 32 nodes ----
+    // ---- 3b. f^eq coefficients: 8 threads per cell share the 16 nodes ----
     {
       const int c = tid >> 3, q = tid & 7;  // 8 threads per cell
       const float ud = cellf[2 * kB2 + c];
@@ -492,8 +492,9 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
 #pragma unroll
       for (int m = 0; m < kMaxM; ++m) { J3[m] = 0.f; J4[m] = 0.f; }
 #pragma unroll
-      for (int i = 0; i < kAeqNodes / 8; ++i)
-        aeq_node<float>(float(tb.gl_t[q + 8 * i]), float(tb.gl_w[q + 8 * i]), A, sh2, uinv,
+      for (int i = 0; i < kAeqNodesF32 / 8; ++i)  // the 16-node rule (N_Omega <= 7 here)
+        aeq_node<float>(float(tb.gl_t[kAeqNodes + q + 8 * i]),
+                        float(tb.gl_w[kAeqNodes + q + 8 * i]), A, sh2, uinv,
                         at_rest, g.nm, J3, J4);
 #pragma unroll
       for (int o = 4; o >= 1; o >>= 1)
