@@ -31,6 +31,9 @@ namespace rslb {
 constexpr int kMaxQL = 8;
 constexpr int kHalo = 4;
 constexpr int kMaxMP = 16;  // kMaxM rounded up to a whole number of 16-byte vectors
+// Up to this many velocities each moment is summed by one lane over all rows;
+// above it the lanes of a warp take rows and a warp reduction follows.
+constexpr int kSerialMomentRows = 128;
 
 template <typename T> struct V16;
 template <> struct V16<float> {
@@ -330,8 +333,31 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
 
   const bool collide = g.tau_mode != kTauNone;
   if (collide) {
-    // ---- 2. moments: warp = 16-byte chunk of cells, lanes = rows ----
-    if (warp < CH) {
+    // ---- 2. moments ----
+    if (V <= kSerialMomentRows) {
+      // few velocities: lane 5c + q of warp w sums moment q of cell w VN + c
+      // over every row by itself (blocks of four rows, then compensated), so
+      // no cross-lane reduction is needed
+      const int c = lane / 5, q = lane - 5 * (lane / 5);
+      if (warp < CH && lane < VN * 5) {
+        const T* col = tile + kHalo + warp * VN + c;
+        const T* wq = tb.mw + (size_t)q * V;
+        Acc<T> acc;
+        int v = 0;
+        for (; v + 4 <= V; v += 4) {
+          T blk = col[v * P] * wq[v];
+          blk += col[(v + 1) * P] * wq[v + 1];
+          blk += col[(v + 2) * P] * wq[v + 2];
+          blk += col[(v + 3) * P] * wq[v + 3];
+          acc.add(blk);
+        }
+        T blk = T(0);
+        for (; v < V; ++v) blk += col[v * P] * wq[v];
+        acc.add(blk);
+        msum[q * B + warp * VN + c] = acc.value();
+      }
+    } else if (warp < CH) {
+      // warp = 16-byte chunk of cells, lanes = rows
       Acc<T> acc[VN][5];
       for (int v0 = lane; v0 < V; v0 += 128) {
         T blk[VN][5];
