@@ -299,7 +299,6 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
   constexpr int W = B + 2 * kHalo;
   constexpr int P = tile_pitch<T>(W);
   constexpr int CH = B / VN;  // 16-byte chunks of interior cells
-  static_assert(CH <= NT / 32, "one warp per interior chunk in the moment phase");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int V = g.V;
   const SodSmem<T> lay(V, B, g.QL, g.nm, nseg > 1);
@@ -335,12 +334,13 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
   if (collide) {
     // ---- 2. moments ----
     if (V <= kSerialMomentRows) {
-      // few velocities: lane 5c + q of warp w sums moment q of cell w VN + c
-      // over every row by itself (blocks of four rows, then compensated), so
-      // no cross-lane reduction is needed
+      // few velocities: lane 5c + q sums moment q of cell c of the warp's
+      // 16-byte chunk over every row by itself (blocks of four rows, then
+      // compensated), so no cross-lane reduction is needed
       const int c = lane / 5, q = lane - 5 * (lane / 5);
-      if (warp < CH && lane < VN * 5) {
-        const T* col = tile + kHalo + warp * VN + c;
+      for (int ch = warp; ch < CH; ch += NT / 32) {
+        if (lane >= VN * 5) break;
+        const T* col = tile + kHalo + ch * VN + c;
         const T* wq = tb.mw + (size_t)q * V;
         Acc<T> acc;
         int v = 0;
@@ -354,10 +354,11 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
         T blk = T(0);
         for (; v < V; ++v) blk += col[v * P] * wq[v];
         acc.add(blk);
-        msum[q * B + warp * VN + c] = acc.value();
+        msum[q * B + ch * VN + c] = acc.value();
       }
-    } else if (warp < CH) {
-      // warp = 16-byte chunk of cells, lanes = rows
+    } else {
+      // warp = 16-byte chunk of cells (warps loop over the chunks), lanes = rows
+      for (int ch = warp; ch < CH; ch += NT / 32) {
       Acc<T> acc[VN][5];
       for (int v0 = lane; v0 < V; v0 += 128) {
         T blk[VN][5];
@@ -370,7 +371,7 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
           const int v = v0 + 32 * u;
           if (v < V) {
             T x[VN];
-            ld_chunk<T>(tile + v * P + kHalo + warp * VN, x);
+            ld_chunk<T>(tile + v * P + kHalo + ch * VN, x);
             T w[5];
 #pragma unroll
             for (int q = 0; q < 5; ++q) w[q] = tb.mw[q * V + v];
@@ -409,7 +410,7 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
         tr_level<1>(h, lo, lane);
         if (lane < VN * 5) {
           const int c = lane / 5, q = lane - 5 * (lane / 5);
-          msum[q * B + warp * VN + c] = (double)h[0] + (double)lo[0];
+          msum[q * B + ch * VN + c] = (double)h[0] + (double)lo[0];
         }
       } else {
 #pragma unroll
@@ -417,8 +418,9 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
 #pragma unroll
           for (int q = 0; q < 5; ++q) {
             const double s = warp_sum(acc[c][q].value());
-            if (lane == 0) msum[q * B + warp * VN + c] = s;
+            if (lane == 0) msum[q * B + ch * VN + c] = s;
           }
+      }
       }
     }
     __syncthreads();
@@ -632,10 +634,12 @@ static int pick_nseg(int V, int B, int NT, int VN) {
 // Opt every stage kernel into the large dynamic shared-memory carve-out
 // (done once at set-up, outside any stream capture).
 cudaError_t sod_set_attributes() {
-  const void* fns[] = {(const void*)sod_stage_kernel<float, 32, 320>,
+  const void* fns[] = {(const void*)sod_stage_kernel<float, 64, 320>,
+                       (const void*)sod_stage_kernel<float, 32, 320>,
                        (const void*)sod_stage_kernel<float, 16, 320>,
                        (const void*)sod_stage_kernel<double, 16, 320>,
                        (const void*)sod_stage_kernel<double, 8, 320>,
+                       (const void*)sod_batch_kernel<float, 64, 320>,
                        (const void*)sod_batch_kernel<float, 32, 320>,
                        (const void*)sod_batch_kernel<float, 16, 320>,
                        (const void*)sod_batch_kernel<double, 16, 320>,
@@ -655,6 +659,11 @@ SodLaunch sod_pick_launch(bool fp64, int V, int QL, int nm, int max_smem) {
     // packed FP32x2 kernel: whole rows per thread, so it needs enough rows to
     // fill a CTA, N_Omega <= 7, and two CTAs per SM
     if (V >= 128 && nm <= 8 && sod32_smem_bytes(V, QL) <= half) return {kSod32Cells, 0};
+    // few velocities: 64-cell tiles share each tile's fixed costs among more
+    // cells and give the row segments 8 cells (V = 24: 0.18 against 0.26 ms
+    // per step of 65536 cells with 32-cell tiles)
+    if (V < 128 && smem_for<float, 64, 320>(V, QL, nm, pick_nseg(V, 64, 320, 4)) <= half)
+      return {64, 0};
     const int n32 = pick_nseg(V, 32, 320, 4), n16 = pick_nseg(V, 16, 320, 4);
     if (smem_for<float, 32, 320>(V, QL, nm, n32) <= half) return {32, 0};
     if (smem_for<float, 16, 320>(V, QL, nm, n16) <= half) return {16, 0};
@@ -696,6 +705,9 @@ cudaError_t sod_stage_launch(const SodLaunch& L, const SodGeom& g, const SodTabl
     if (L.B == kSod32Cells) return sod32_stage_launch(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
   }
   switch (L.B) {
+    case 64:
+      if constexpr (sizeof(T) == 4) return launch_b<T, 64>(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
+      break;
     case 32:
       if constexpr (sizeof(T) == 4) return launch_b<T, 32>(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
       break;
@@ -720,6 +732,7 @@ template cudaError_t sod_stage_launch<double>(const SodLaunch&, const SodGeom&,
 size_t sod_stage_smem_bytes(bool fp64, int B, int V, int QL, int nm) {
   if (!fp64) {
     if (B == kSod32Cells) return sod32_smem_bytes(V, QL);
+    if (B == 64) return smem_for<float, 64, 320>(V, QL, nm, pick_nseg(V, 64, 320, 4));
     if (B == 32) return smem_for<float, 32, 320>(V, QL, nm, pick_nseg(V, 32, 320, 4));
     if (B == 16) return smem_for<float, 16, 320>(V, QL, nm, pick_nseg(V, 16, 320, 4));
   } else {
@@ -743,6 +756,11 @@ cudaError_t sod_batch_stage_launch(int B, size_t smem, int grid, const SodRunDes
   if constexpr (sizeof(T) == 4) {
     if (B == kSod32Cells)
       return sod32_batch_launch(smem, grid, runs, tasks, ntasks, step, stage, err, maps, st);
+    if (B == 64) {
+      sod_batch_kernel<T, 64, 320><<<grid, 320, smem, st>>>(runs, tasks, ntasks, step, stage, err,
+                                                           pick_nseg(V, 64, 320, 4));
+      return cudaGetLastError();
+    }
     if (B == 32) {
       sod_batch_kernel<T, 32, 320><<<grid, 320, smem, st>>>(runs, tasks, ntasks, step, stage, err,
                                                            pick_nseg(V, 32, 320, 4));

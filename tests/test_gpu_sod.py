@@ -116,12 +116,15 @@ def test_large_velocity_sets(precision, tol, Q_xi):
     sodcase.compare(case, 6, precision, tol, tol if precision == "f64" else None)
 
 
-@pytest.mark.parametrize("precision,tiles,tol", [("f32", (PACKED, 32, 16), 1e-6),
-                                                 ("f64", (16, 8), 1e-13)])
-def test_tile_width_does_not_change_results(precision, tiles, tol):
+@pytest.mark.parametrize("precision,tiles,tol,Q_xi", [("f32", (PACKED, 64, 32, 16), 1e-6, 100),
+                                                      ("f32", (64, 32, 16), 1e-6, 8),
+                                                      ("f64", (16, 8), 1e-13, 100),
+                                                      ("f64", (16, 8), 1e-13, 8)])
+def test_tile_width_does_not_change_results(precision, tiles, tol, Q_xi):
+    """V = 300 and V = 24 (moments summed per lane below 128 velocities)."""
     from paper_1612_01287_gb300 import Sod
     case = sodcase.gpu_kwargs(small_case())
-    case.update(Z=200, Q_xi=100)
+    case.update(Z=200, Q_xi=Q_xi)
     out = []
     for B in tiles:
         with Sod(precision=precision, tile_cells=B, **case) as s:
