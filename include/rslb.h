@@ -119,7 +119,7 @@ typedef struct rslb_config {
   const double* beta0;
   /* Cells per CTA tile of the stage kernel: 0 = automatic; otherwise
    * RSLB_PACKED_TILE_CELLS (the packed FP32x2 kernel: V >= 128,
-   * N_Omega <= 7), 64, 32 or 16 (RSLB_F32), 16 or
+   * N_Omega <= 7), 128, 64, 32 or 16 (RSLB_F32), 16 or
    * 8 (RSLB_F64).  A tuning knob; results agree to rounding. */
   int tile_cells;
 } rslb_config;

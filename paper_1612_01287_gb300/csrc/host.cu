@@ -352,11 +352,11 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
   if (c.tile_cells != 0) {
     // explicit tile width (tuning): must be one the kernels are built for
     const bool okB = fp64 ? (c.tile_cells == 16 || c.tile_cells == 8)
-                          : (c.tile_cells == kSod32Cells || c.tile_cells == 64 ||
+                          : (c.tile_cells == kSod32Cells || c.tile_cells == 128 || c.tile_cells == 64 ||
                              c.tile_cells == 32 || c.tile_cells == 16);
     if (!okB)
       return set_error(RSLB_ERR_ARG, "rslb_init: tile_cells must be 0 or one of %s",
-                       fp64 ? "16, 8" : "the packed width, 64, 32, 16");
+                       fp64 ? "16, 8" : "the packed width, 128, 64, 32, 16");
     if (c.tile_cells == kSod32Cells && (V < 128 || nm > 8))
       return set_error(RSLB_ERR_ARG,
                        "rslb_init: the packed tile width needs V >= 128 and N_Omega <= 7");
@@ -859,7 +859,7 @@ int batch_build_classes(rslb_sod_batch* b, int autotune) {
     }
     std::vector<int> cands = {cachedB ? cachedB : c.B};
     if (autotune && !cachedB) {
-      const int alt[] = {kSod32Cells, 64, 32, 16, 8};
+      const int alt[] = {kSod32Cells, 128, 64, 32, 16, 8};
       for (int B : alt)
         if (B != c.B && sod_stage_smem_bytes(b->fp64, B, V, QL, nm) > 0 &&
             sod_stage_smem_bytes(b->fp64, B, V, QL, nm) <= (size_t)max_smem &&

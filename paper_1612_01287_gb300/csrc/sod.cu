@@ -634,11 +634,13 @@ static int pick_nseg(int V, int B, int NT, int VN) {
 // Opt every stage kernel into the large dynamic shared-memory carve-out
 // (done once at set-up, outside any stream capture).
 cudaError_t sod_set_attributes() {
-  const void* fns[] = {(const void*)sod_stage_kernel<float, 64, 320>,
+  const void* fns[] = {(const void*)sod_stage_kernel<float, 128, 320>,
+                       (const void*)sod_stage_kernel<float, 64, 320>,
                        (const void*)sod_stage_kernel<float, 32, 320>,
                        (const void*)sod_stage_kernel<float, 16, 320>,
                        (const void*)sod_stage_kernel<double, 16, 320>,
                        (const void*)sod_stage_kernel<double, 8, 320>,
+                       (const void*)sod_batch_kernel<float, 128, 320>,
                        (const void*)sod_batch_kernel<float, 64, 320>,
                        (const void*)sod_batch_kernel<float, 32, 320>,
                        (const void*)sod_batch_kernel<float, 16, 320>,
@@ -659,9 +661,11 @@ SodLaunch sod_pick_launch(bool fp64, int V, int QL, int nm, int max_smem) {
     // packed FP32x2 kernel: whole rows per thread, so it needs enough rows to
     // fill a CTA, N_Omega <= 7, and two CTAs per SM
     if (V >= 128 && nm <= 8 && sod32_smem_bytes(V, QL) <= half) return {kSod32Cells, 0};
-    // few velocities: 64-cell tiles share each tile's fixed costs among more
-    // cells and give the row segments 8 cells (V = 24: 0.18 against 0.26 ms
-    // per step of 65536 cells with 32-cell tiles)
+    // few velocities: wide tiles share each tile's fixed costs among more
+    // cells and give the row segments more cells (65536 cells, V = 24: 0.15 ms
+    // per step with 128-cell tiles, 0.18 with 64, 0.26 with 32)
+    if (V < 48 && smem_for<float, 128, 320>(V, QL, nm, pick_nseg(V, 128, 320, 4)) <= half)
+      return {128, 0};
     if (V < 128 && smem_for<float, 64, 320>(V, QL, nm, pick_nseg(V, 64, 320, 4)) <= half)
       return {64, 0};
     const int n32 = pick_nseg(V, 32, 320, 4), n16 = pick_nseg(V, 16, 320, 4);
@@ -705,6 +709,9 @@ cudaError_t sod_stage_launch(const SodLaunch& L, const SodGeom& g, const SodTabl
     if (L.B == kSod32Cells) return sod32_stage_launch(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
   }
   switch (L.B) {
+    case 128:
+      if constexpr (sizeof(T) == 4) return launch_b<T, 128>(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
+      break;
     case 64:
       if constexpr (sizeof(T) == 4) return launch_b<T, 64>(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
       break;
@@ -732,6 +739,7 @@ template cudaError_t sod_stage_launch<double>(const SodLaunch&, const SodGeom&,
 size_t sod_stage_smem_bytes(bool fp64, int B, int V, int QL, int nm) {
   if (!fp64) {
     if (B == kSod32Cells) return sod32_smem_bytes(V, QL);
+    if (B == 128) return smem_for<float, 128, 320>(V, QL, nm, pick_nseg(V, 128, 320, 4));
     if (B == 64) return smem_for<float, 64, 320>(V, QL, nm, pick_nseg(V, 64, 320, 4));
     if (B == 32) return smem_for<float, 32, 320>(V, QL, nm, pick_nseg(V, 32, 320, 4));
     if (B == 16) return smem_for<float, 16, 320>(V, QL, nm, pick_nseg(V, 16, 320, 4));
@@ -756,6 +764,11 @@ cudaError_t sod_batch_stage_launch(int B, size_t smem, int grid, const SodRunDes
   if constexpr (sizeof(T) == 4) {
     if (B == kSod32Cells)
       return sod32_batch_launch(smem, grid, runs, tasks, ntasks, step, stage, err, maps, st);
+    if (B == 128) {
+      sod_batch_kernel<T, 128, 320><<<grid, 320, smem, st>>>(runs, tasks, ntasks, step, stage, err,
+                                                            pick_nseg(V, 128, 320, 4));
+      return cudaGetLastError();
+    }
     if (B == 64) {
       sod_batch_kernel<T, 64, 320><<<grid, 320, smem, st>>>(runs, tasks, ntasks, step, stage, err,
                                                            pick_nseg(V, 64, 320, 4));

@@ -117,7 +117,7 @@ def test_large_velocity_sets(precision, tol, Q_xi):
 
 
 @pytest.mark.parametrize("precision,tiles,tol,Q_xi", [("f32", (PACKED, 64, 32, 16), 1e-6, 100),
-                                                      ("f32", (64, 32, 16), 1e-6, 8),
+                                                      ("f32", (128, 64, 32, 16), 1e-6, 8),
                                                       ("f64", (16, 8), 1e-13, 100),
                                                       ("f64", (16, 8), 1e-13, 8)])
 def test_tile_width_does_not_change_results(precision, tiles, tol, Q_xi):
