@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tubes", type=int, default=len(TAUS),
                     help="number of the four tau tubes per step (profiling runs use 1)")
@@ -548,7 +548,7 @@ def run_ours(args, rank, world, local_rank):
                     t.set_state_ptr(hf.data_ptr(), 0)
                     t.step(1)
 
-    e2e_run(1)  # warm-up
+    e2e_run(2)  # warm-up
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
     barrier()
     t0 = time.perf_counter()
