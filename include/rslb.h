@@ -158,7 +158,11 @@ int rslb_sync(rslb_handle* h);
 
 /*
  * Per-cell macroscopic fields of the current state, in FP64, layout
- * out[field*Z + s] with the RSLB_FIELD_* order (RSLB_NFIELDS fields).
+ * out[field*Z + s] with the RSLB_FIELD_* order (RSLB_NFIELDS fields): the
+ * moments N^mu, T^{mu nu} of the populations (Eq. macro_jk) and the Landau
+ * frame quantities n, E, P, T, beta, gamma, lambda_bar, q, Pi (Sec. II E,
+ * Eqs. E_landau-pi_val).  For FP32 populations the sums are formed as exact
+ * products summed in double-float arithmetic.
  * out: caller-owned, host memory if out_on_device == 0, else device memory
  * on the handle's device.  Synchronises the stream.
  * Errors: RSLB_ERR_ARG, RSLB_ERR_CUDA, RSLB_ERR_NONPHYSICAL.
