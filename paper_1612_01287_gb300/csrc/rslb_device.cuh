@@ -105,14 +105,19 @@ __device__ __forceinline__ LandauOut landau_factored(double Np, double Nm, doubl
                                                      double Am, double D) {
   LandauOut o;
   const double a = sqrt(Ap), b = sqrt(Am);
-  const double sab = sqrt(a * b);
-  const double h = 0.5 / sab;
-  o.E = 0.5 * (D + a * b);
-  o.beta = (a - b) / (a + b);
-  o.gamma = (a + b) * h;
+  const double ab = a * b, apb = a + b;
+  const double sab = sqrt(ab);
+  const double X = b * Np + a * Nm;
+  // one FP64 division (slow on this part) gives 1/(2 sqrt(ab)), 1/(a+b) and
+  // 1/X: r = 1/(sqrt(ab) (a+b) X)
+  const double r = 1.0 / (sab * apb * X);
+  const double h = 0.5 * apb * X * r;  // 1/(2 sqrt(ab))
+  o.E = 0.5 * (D + ab);
+  o.beta = (a - b) * sab * X * r;      // (a - b)/(a + b)
+  o.gamma = apb * h;
   o.u = fabs(a - b) * h;
-  o.n = (b * Np + a * Nm) * h;
-  o.T = o.E / (3.0 * o.n);
+  o.n = X * h;
+  o.T = (2.0 / 3.0) * o.E * ab * apb * r;  // E/(3n) = 2 E sqrt(ab)/(3X)
   o.ok = (Ap > 0.0) && (Am > 0.0) && (o.E > 0.0) && (o.n > 0.0) && isfinite(o.E) &&
          isfinite(o.n) && isfinite(o.beta) && (fabs(o.beta) < 1.0);
   return o;
