@@ -1,7 +1,6 @@
 """CPU checks of the C ABI: the library builds for sm_103a, loads, exports every
 function that include/rslb.h declares, and the host-side parts (quadrature,
 argument validation) behave as documented.  No GPU compute is launched."""
-import ctypes
 import os
 import re
 

@@ -2,7 +2,6 @@
 facts that do not come from it: finite differences, exact moment
 preservation of the restriction, exactness on equilibria whose Legendre
 content fits the low-order set, and the conservation property."""
-import math
 
 import numpy as np
 import pytest

@@ -1,7 +1,6 @@
 """Learned closure on the GPU against the FP64 reference (oracle/closure.py):
 restriction, MLP forward, backward (gradient) and the conserving correction;
 then a small end-to-end training run that must lower the low-order error."""
-import math
 
 import numpy as np
 import pytest

@@ -4,7 +4,6 @@ Tolerances: the FP64 path must match to 1e-12 and the FP32 path to 1e-5 in
 the max-normalised error max_s|a-b|/max_s|b| on n, E, beta and Pi (the shear
 stress of Eq. pi_val); FP64 populations are also compared element by element.
 """
-import math
 
 import numpy as np
 import pytest
