@@ -39,7 +39,7 @@ BYTES_PER_CV_STEP_F32 = 32  # stage 1 r+w (8 B), stages 2-3 read f_n, f^(i), wri
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -99,10 +99,14 @@ def config_dict(w, dt, ntubes=len(TAUS)):
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi samples every 50 ms; stop() keeps those taken inside the window
+    marked by region_begin()/region_end() (all of them if none falls inside)."""
+
     def __init__(self, index=0):
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -111,14 +115,53 @@ class ClockSampler:
             self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
-                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "--query-gpu=timestamp,clocks.sm,clocks.max.sm,power.draw,"
                  "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def region_begin(self):
+        self.t0 = time.time()
+
+    def region_end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def parse(lines, t0=None, t1=None):
+        """Summary of nvidia-smi CSV lines (timestamp first); samples outside
+        [t0, t1] are dropped when some fall inside."""
+        import datetime
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
+        for line in lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rec = (float(parts[1]), float(parts[2]), parts[5:9])
+            except ValueError:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            rows.append((ts, rec))
+        inside = [r for ts, r in rows
+                  if t0 is not None and t1 is not None and ts is not None and t0 <= ts <= t1]
+        use = inside if inside else [r for _, r in rows]
+        if not use:
+            return None
+        reasons = set()
+        for _, _, flags in use:
+            for n, v in zip(names, flags):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in use), "sm_max_mhz": max(r[1] for r in use),
+                "samples": len(use), "in_timed_region": bool(inside), "reasons": sorted(reasons)}
 
     def stop(self):
         if self.proc is None:
@@ -129,28 +172,12 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
+        out = self.parse(open(self.path), self.t0, self.t1)
         try:
             os.remove(self.path)
         except OSError:
             pass
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "samples": len(sm), "reasons": sorted(reasons)}
+        return out
 
 
 # --------------------------------------------------------------------------- helpers
@@ -505,6 +532,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
+    clk.region_begin()
     start.record(stream)
     for ts in tstreams:
         ts.wait_event(start)
@@ -517,6 +545,7 @@ def run_ours(args, rank, world, local_rank):
         stream.wait_event(e)
     end.record(stream)
     barrier()
+    clk.region_end()
     clocks = clk.stop()
     ms = start.elapsed_time(end)
     ms = max_over_ranks(ms, dist, "cuda")
