@@ -211,12 +211,37 @@ def source_sha(kernel="sod32_stage_kernel"):
         csrc = os.path.join(ROOT, "paper_1612_01287_gb300", "csrc")
         files = [os.path.join("paper_1612_01287_gb300", "csrc", f) for f in sorted(os.listdir(csrc))]
     for f in files:
-        data = open(os.path.join(ROOT, f), "rb").read()
+        text = open(os.path.join(ROOT, f), encoding="utf-8").read()
         pat = KERNEL_SOURCE_LINES.get(f)
         if pat is not None:
-            data = b"".join(l for l in data.splitlines(True) if pat.match(l.decode()))
-        h.update(data)
+            text = "".join(l for l in text.splitlines(True) if pat.match(l))
+        h.update(" ".join(_strip_comments(text).split()).encode())
     return h.hexdigest()[:16]
+
+
+def _strip_comments(text):
+    """C/C++ source without its comments (the recorded traffic follows the
+    code, not the prose; the caller also collapses white space); string
+    literals are kept as they are."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        ch = text[i]
+        if ch == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(ch)
+            i += 1
+    return "".join(out)
 
 
 def recorded_traffic(kernel):

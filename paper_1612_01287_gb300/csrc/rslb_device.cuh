@@ -12,9 +12,10 @@ namespace rslb {
 
 constexpr int kMaxM = 13;    // N_Omega <= 12
 constexpr int kAeqNodes = 32;  // Gauss-Legendre nodes for the a_{l,m} integrals
-// The FP32 stage kernels use a 16-node rule for N_Omega <= 7: it agrees with
-// the 32-node rule to ~1e-13 of a_{l,0} for m <= 7 and u up to 100.  The node
-// table holds the 32-node rule and then the 16-node one.
+// The FP32 stage kernels use a 16-node rule for N_Omega <= 7: for m <= 7 it
+// agrees with the exact a_{l,m} to 2e-14 of a_{l,0} up to u = 20 and to 5e-13
+// at u = 50, far inside FP32.  The node table holds the 32-node rule and then
+// the 16-node one.
 constexpr int kAeqNodesF32 = 16;
 constexpr int kAeqTable = kAeqNodes + kAeqNodesF32;
 

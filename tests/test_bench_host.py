@@ -1,6 +1,6 @@
 """Host-side parts of bench.py that need no GPU: the clock summary keeps only
 the nvidia-smi samples taken inside the timed region, and the DRAM-traffic
-record is keyed to the kernel's sources (comments elsewhere in the C header
+record is keyed to the kernel's code (comments and the rest of the C header
 do not void it)."""
 import datetime
 import os
@@ -47,6 +47,9 @@ def test_traffic_key_ignores_header_comments(tmp_path, monkeypatch):
     base = bench.source_sha("sod32_stage_kernel")
     hdr = files["include/rslb.h"]
     hdr.write_text(hdr.read_text() + "\n/* a comment */\n")
+    assert bench.source_sha("sod32_stage_kernel") == base
+    dev = files["paper_1612_01287_gb300/csrc/rslb_device.cuh"]
+    dev.write_text(dev.read_text().replace("namespace rslb {", "// reworded\n// note\nnamespace rslb {", 1))
     assert bench.source_sha("sod32_stage_kernel") == base
     hdr.write_text(hdr.read_text().replace("#define RSLB_PACKED_TILE_CELLS 28",
                                            "#define RSLB_PACKED_TILE_CELLS 20"))
