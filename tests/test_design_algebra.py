@@ -67,3 +67,54 @@ def test_landau_with_one_division(n, T, beta, seed):
     for k in ("n", "E", "T", "gamma"):
         assert abs(got[k] - ref[k]) <= 1e-13 * abs(ref[k]), k
     assert abs(got["beta"] - ref["beta"]) <= 1e-13
+
+
+def test_weno_scale_from_exponent_bits():
+    """2^(127-e) from an AND and a subtract on the FP32 bits (and the FP64
+    analogue) brings a normal maximum into [1, 2) exactly; zero and subnormal
+    maxima get the largest such power (the kernels' WENO scale)."""
+    rng = np.random.default_rng(5)
+    m32 = np.float32(10.0) ** rng.uniform(-37, 37, 1000).astype(np.float32)
+    inv32 = (np.uint32(0x7F000000) - (m32.view(np.uint32) & np.uint32(0x7F800000))).view(np.float32)
+    r = m32 * inv32
+    assert np.all((r >= 1.0) & (r < 2.0))
+    assert np.all(inv32 == np.float32(2.0) ** (-np.floor(np.log2(m32.astype(np.float64)))).astype(np.float32))
+    z = np.array([0.0, 1e-40], dtype=np.float32)
+    zinv = (np.uint32(0x7F000000) - (z.view(np.uint32) & np.uint32(0x7F800000))).view(np.float32)
+    assert np.all(zinv == np.float32(2.0) ** 127)
+    m64 = 10.0 ** rng.uniform(-300, 300, 1000)
+    inv64 = (np.uint64(0x7FE0000000000000) -
+             (m64.view(np.uint64) & np.uint64(0x7FF0000000000000))).view(np.float64)
+    r64 = m64 * inv64
+    assert np.all((r64 >= 1.0) & (r64 < 2.0))
+
+
+def test_double_float_moment_sums():
+    """The FP32 output-moment kernel's accumulation: the FP64 weight split as
+    w_hi + w_lo (FP32), f w_hi formed exactly as product + fma remainder, hi
+    parts added with TwoSum, remainders and errors in a plain FP32 low sum.
+    Emulated step by step in FP32 (the remainder is exact, so evaluating it in
+    FP64 is exact too); the result agrees with the exact sum to ~1e-14 (the
+    low sum's own FP32 rounding over V terms bounds it by about V 2^-48)."""
+    from fractions import Fraction
+    rng = np.random.default_rng(9)
+    V = 600
+    f = rng.uniform(0.0, 1.0, V).astype(np.float32) * np.float32(1e-2)
+    x, p = np.linspace(-0.99, 0.99, V), np.repeat([0.4, 2.2, 6.1], V // 3)
+    w = p * (1 + x) ** 2
+    wh = w.astype(np.float32)
+    wl = (w - wh.astype(np.float64)).astype(np.float32)
+    H = np.float32(0.0)
+    L = np.float32(0.0)
+    for fv, a, b in zip(f, wh, wl):
+        ph = np.float32(fv * a)
+        pl = np.float32(np.float64(fv) * np.float64(a) - np.float64(ph))  # exact remainder
+        pl = np.float32(np.float64(fv) * np.float64(b) + np.float64(pl))   # fma(f, wl, pl)
+        s = np.float32(H + ph)
+        bp = np.float32(s - H)
+        e = np.float32(np.float32(H - np.float32(s - bp)) + np.float32(ph - bp))
+        H = s
+        L = np.float32(L + np.float32(e + pl))
+    got = float(H) + float(L)
+    exact = sum(Fraction(float(fv)) * Fraction(float(wv)) for fv, wv in zip(f, w))
+    assert abs(Fraction(got) - exact) <= Fraction(5, 10 ** 14) * abs(exact)
