@@ -118,3 +118,39 @@ def test_double_float_moment_sums():
     got = float(H) + float(L)
     exact = sum(Fraction(float(fv)) * Fraction(float(wv)) for fv, wv in zip(f, w))
     assert abs(Fraction(got) - exact) <= Fraction(5, 10 ** 14) * abs(exact)
+
+
+def _kp_entry_from_table(Q, xi, w, j, jp):
+    """One K^P entry the way the GPU set-up builds it (Eq. K_leg_disc): the
+    m-dependent factors of both sums and of both Legendre recurrences come
+    from a per-m table, P_m(xi_j) advances by Bonnet's recurrence and the
+    xi_j' values are carried as a window P_{m-2} .. P_{m+2}."""
+    c = np.zeros((Q, 7))
+    for m in range(Q):
+        d = float(m)
+        c[m] = [d * (d + 1) * (d + 2) / (2 * (2 * d + 3)),
+                0.5 * d * (d + 1) * (2 * d + 1) / ((2 * d - 1) * (2 * d + 3)) if m else 0.0,
+                0.5 * d * (d + 1) * (d - 1) / (2 * d - 1) if m else 0.0,
+                (2 * d + 1) / (d + 1), d / (d + 1), (2 * d + 5) / (d + 3), (d + 2) / (d + 3)]
+    x, y = xi[j], xi[jp]
+    px, pxm1 = x, 1.0
+    ym2, ym1, y0 = 0.0, 1.0, y
+    yp1 = 0.5 * (3 * y * y - 1)
+    yp2 = (5 * y * yp1 - 2 * y0) / 3
+    s1 = s2 = 0.0
+    for m in range(1, Q):
+        if m <= Q - 3:
+            s1 += c[m, 0] * px * yp2
+        s2 += px * (c[m, 1] * y0 + c[m, 2] * ym2)
+        px, pxm1 = c[m, 3] * x * px - c[m, 4] * pxm1, px
+        yn = c[m, 5] * y * yp2 - c[m, 6] * yp1
+        ym2, ym1, y0, yp1, yp2 = ym1, y0, yp1, yp2, yn
+    return w[j] * (s1 - s2)
+
+
+@pytest.mark.parametrize("Q", [8, 20, 41])
+def test_kp_from_the_coefficient_table(Q):
+    xi, w = oracle.gauss_legendre(Q)
+    K = oracle.kp_matrix(Q)
+    got = np.array([[_kp_entry_from_table(Q, xi, w, j, jp) for jp in range(Q)] for j in range(Q)])
+    assert np.abs(got - K).max() <= 1e-12 * np.abs(K).max()
