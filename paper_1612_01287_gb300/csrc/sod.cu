@@ -1,15 +1,16 @@
 // sod.cu -- fused RK-stage kernel of the R-SLB Sod shock tube (sm_103a).
 //
-// One CTA owns a tile of B consecutive cells and all V velocities.  A stage
-// (Eq. rk3) is one launch:
+// One CTA owns a tile of B consecutive cells (128, 64, 32 or 16 for FP32, 16
+// or 8 for FP64) and all V velocities.  A stage (Eq. rk3) is one launch:
 //   1. the tile plus a 4-cell halo on each side is staged in shared memory
 //      with 16-byte cp.async copies (velocity-major rows; boundary tiles map
 //      out-of-domain cells through the boundary condition);
-//   2. moments: each warp owns a 16-byte column chunk of cells and its lanes
-//      own velocity rows; the five sums of the factored Landau form are
-//      accumulated in blocks of four rows and the blocks are added with Kahan
-//      compensation (FP32), then a warp-shuffle tree in FP64 reduces them
-//      across the velocity set;
+//   2. moments: the five sums of the factored Landau form.  Up to 128
+//      velocities one lane per (cell, sum) adds every row itself (blocks of
+//      four rows, Kahan-compensated in FP32); above that each warp owns a
+//      16-byte column chunk of cells, its lanes own velocity rows, and an
+//      error-free FP32 transposing warp reduction (FP64 shuffles for FP64
+//      populations) combines the lanes;
 //   3. per cell: Landau matching in FP64 (Sec. II E), the relaxation time, and
 //      the f^eq expansion coefficients (Sec. III D) by a Gauss-Legendre rule
 //      spread over the CTA and reduced by shuffles;
@@ -18,7 +19,9 @@
 //      that a sliding window shares them between neighbouring faces; f^eq
 //      from the per-cell coefficients; Anderson-Witting relaxation
 //      (Eq. L_Sod); the RK combination.  Rows are visited negative-xi first so
-//      that the upwind direction is uniform within a warp;
+//      that the upwind direction is uniform within a warp; with few
+//      velocities each row is split into segments of B/2 .. B/8 cells so that
+//      enough threads have work;
 //   5. vectorised, coalesced store of the tile interior (with the f_n term of
 //      stages 2 and 3).
 // Shared-memory rows have a pitch whose 16-byte count is odd, so the 16-byte
