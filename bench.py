@@ -87,6 +87,14 @@ def workload_dt(w):
     return w["cfl"] * w["dz"] / float(np.abs(xi).max())
 
 
+def oracle_workload_dt(w):
+    """The same time step from the oracle's own Gauss-Legendre nodes (the CPU
+    legs depend on oracle/ alone)."""
+    import oracle
+    xi, _ = oracle.gauss_legendre(w["Q_xi"])
+    return w["cfl"] * w["dz"] / float(np.abs(xi).max())
+
+
 def config_dict(w, dt, ntubes=len(TAUS)):
     taus = ",".join("%g" % t for t in TAUS[:ntubes])
     return {"workload": "sod_shock_tube_Nx%d_NL%d_Nxi%d_tau{%s}" % (
@@ -431,12 +439,12 @@ def bench_closure(stream):
     return out
 
 
-def cpu_baseline(w, dt, steps=20, cells=2048):
-    """The FP64 oracle on the host cores, on a bounded sample of the workload:
-    `cells` cells around the membrane of one tube, all 600 velocities."""
+def _oracle_window(job):
+    """One process of a CPU leg: the FP64 oracle advances `cells` cells of one tube
+    (tau = 1e-2, all velocities; the window starts at cell `lo`, outflow ends) by
+    `warmup` untimed and `steps` timed RK3 steps; returns the timed seconds."""
+    w, lo, cells, dt, steps, warmup = job
     import oracle
-    Z = w["Z"]
-    lo = Z // 2 - cells // 2
     dz = w["dz"]
     zc = -1.0 + (np.arange(lo, lo + cells) + 0.5) * dz
     (nL, TL, bL), (nR, TR, bR) = w["left"], w["right"]
@@ -445,52 +453,71 @@ def cpu_baseline(w, dt, steps=20, cells=2048):
                           tau=1e-2, dt=dt)
     f = oracle.sod_init_fields(p, np.where(zc < 0, nL, nR), np.where(zc < 0, TL, TR),
                                np.where(zc < 0, bL, bR))
+    if warmup:
+        f = oracle.sod_steps(p, f, warmup)
     t0 = time.perf_counter()
     oracle.sod_steps(p, f, steps)
-    el = time.perf_counter() - t0
-    cvu = cells * w["Q_xi"] * w["Q_L"] * steps
-    return {"value": cvu / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d cells x %d velocities x %d RK3 steps of one tube (tau=1e-2), "
-                      "single-threaded FP64 C oracle, %.1f s" % (cells, w["Q_xi"] * w["Q_L"],
-                                                                 steps, el)}
+    return time.perf_counter() - t0
+
+
+def oracle_rate(w, dt, procs, cells, steps, warmup=0):
+    """Cell-velocity updates/s of the single-threaded oracle run in `procs`
+    processes at once (spawned: this may run after CUDA work), each on its own
+    window of `cells` cells around the membrane; the slowest process sets the
+    time.  Returns (rate, slowest seconds, cell-velocity updates)."""
+    import multiprocessing as mp
+    Z = w["Z"]
+    first = Z // 2 - procs * cells // 2
+    jobs = [(w, first + i * cells, cells, dt, steps, warmup) for i in range(procs)]
+    if procs == 1:
+        times = [_oracle_window(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            times = pool.map(_oracle_window, jobs)
+    cvu = procs * cells * w["Q_xi"] * w["Q_L"] * steps
+    el = max(times)
+    return cvu / el, el, cvu
+
+
+def cpu_baseline(w, steps=20):
+    """The FP64 oracle on the host cores, on bounded samples of the workload: one
+    process on 1024 cells, then one process per core, each on its own 512-cell
+    window around the membrane (the same single-threaded code; windows are
+    independent problems with outflow ends)."""
+    dt = oracle_workload_dt(w)
+    ncores = os.cpu_count() or 1
+    V = w["Q_xi"] * w["Q_L"]
+    one, el1, _ = oracle_rate(w, dt, 1, 1024, steps)
+    allc, elc, cvc = oracle_rate(w, dt, ncores, 512, steps)
+    return {"value": allc, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": "%d processes (one per core) x 512 cells x %d velocities x %d RK3 steps "
+                      "of one tube (tau=1e-2), single-threaded FP64 C oracle in each, %.1f s "
+                      "wall" % (ncores, V, steps, elc),
+            "single_thread": {"value": one, "unit": UNIT, "cores": 1,
+                              "sample": "1024 cells x %d velocities x %d RK3 steps, %.1f s"
+                                        % (V, steps, el1)}}
 
 
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The oracle, as it stands, on all host cores: one process per core, each
+    advancing its own 512-cell window of the tau = 1e-2 tube by one RK3 step per
+    bench step (W untimed, K timed).  Depends on oracle/ alone."""
     if rank != 0:
         return 0
     w = workloads.sod_large()
-    from paper_1612_01287_gb300 import build
-    build.build()
-    dt = workload_dt(w)
-    # each step: the oracle advances a bounded sample by one RK3 step
-    import oracle
+    dt = oracle_workload_dt(w)
+    ncores = os.cpu_count() or 1
     cells = 512
-    Z = w["Z"]
-    lo = Z // 2 - cells // 2
-    dz = w["dz"]
-    zc = -1.0 + (np.arange(lo, lo + cells) + 0.5) * dz
-    (nL, TL, bL), (nR, TR, bR) = w["left"], w["right"]
-    p = oracle.sod_params(cells, w["Q_xi"], w["Q_L"], w["N_Omega"], z_min=-1.0 + lo * dz,
-                          z_max=-1.0 + (lo + cells) * dz, bc="outflow", tau_mode="const",
-                          tau=1e-2, dt=dt)
-    f = oracle.sod_init_fields(p, np.where(zc < 0, nL, nR), np.where(zc < 0, TL, TR),
-                               np.where(zc < 0, bL, bR))
-    for _ in range(args.warmup):
-        f = oracle.sod_steps(p, f, 1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        f = oracle.sod_steps(p, f, 1)
-    el = time.perf_counter() - t0
-    cvu = cells * w["Q_xi"] * w["Q_L"] * args.steps
-    val = cvu / el
-    sample = ("%d cells x %d velocities per step, one RK3 step per bench step, "
-              "single-threaded FP64 C oracle" % (cells, w["Q_xi"] * w["Q_L"]))
+    val, el, _ = oracle_rate(w, dt, ncores, cells, args.steps, warmup=args.warmup)
+    sample = ("%d processes (one per core) x %d cells x %d velocities, one RK3 step per "
+              "bench step, single-threaded FP64 C oracle in each" % (ncores, cells,
+                                                                   w["Q_xi"] * w["Q_L"]))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(w, dt),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": ncores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -692,7 +719,7 @@ def run_ours(args, rank, world, local_rank):
     }
     line.update(extras)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(w, dt)
+        line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -189,8 +189,8 @@ int rslb_time(const rslb_handle* h, double* t, long long* steps);
 int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* threads);
 
 /*
- * Allocation-free shock-tube step (no counterpart in the paper; a service for
- * callers that cannot allocate device memory).
+ * Allocation-free shock-tube step.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory.
  *
  * Some callers may not call cudaMalloc or any allocating routine: code that runs
  * while another component owns all device memory (a framework's caching
@@ -205,8 +205,8 @@ int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* threads);
  *   cfg:    the configuration, as for rslb_init (n0/T0/beta0 and tile_cells
  *           are ignored; the populations come from f);
  *   f:      caller-owned device array of V*Z values in the cfg precision
- *           (f[v*Z + s], v = k*Q_xi + j), advanced in place by nsteps TVD-RK3
- *           steps (Eq. rk3 of L_Sod, Eq. L_Sod);
+ *           (f[v*Z + s], v = k*Q_xi + j), advanced in place by nsteps steps,
+ *           the same TVD-RK3 steps as rslb_step performs;
  *   stream: cudaStream_t as void* (NULL = legacy default stream).
  *
  * Limits: Q_xi*Q_L <= RSLB_NOALLOC_MAX_VELOCITIES, Q_L <= 8, and three stage
@@ -214,7 +214,8 @@ int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* threads);
  * larger problems are rejected with RSLB_ERR_UNSUPPORTED before any device
  * work.  The call synchronises the stream before returning and reports device
  * errors (RSLB_ERR_NONPHYSICAL) directly.
- * The first call on a device looks up the array's device address (once per
+ * The first call on a device looks up the array's device address and opts
+ * the stage kernels into large shared memory on that device (once per
  * device); make that first call before any stream capture.  Every call shares
  * the one array, which keeps the previous call's contents (each call clears
  * what it needs), so calls that overlap on the GPU -- from several threads or
@@ -302,9 +303,6 @@ void rslb_sod_batch_destroy(rslb_sod_batch* b);
 
 #define RSLB_KP_SIMT 0   /* K^P contraction on the CUDA cores in the working
                             precision (FP64 or FP32) */
-#define RSLB_KP_BF16X3 1 /* reserved: BF16 hi/lo split on the tensor cores
-                            (not available: its ~1e-5 error per product is
-                            at the FP32 tolerance; see RSLB_KP_TF32X3) */
 #define RSLB_KP_TF32X3 2 /* K^P contraction on the tcgen05 tensor cores
                             (kind::tf32, accumulators in tensor memory):
                             both operands split x = hi + lo with

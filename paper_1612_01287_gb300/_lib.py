@@ -230,7 +230,7 @@ def sod_step_noalloc(f_ptr, nsteps, Z, Q_xi, Q_L=3, N_Omega=None, z_min=-1.0, z_
 
 BJ_FIELDS = ("tau", "n", "E", "P", "T", "Pi", "PL", "PT")
 GAS = {"parton": 0, "ideal": 1}
-KP = {"simt": 0, "bf16x3": 1, "tf32x3": 2}
+KP = {"simt": 0, "tf32x3": 2}
 
 
 class BjorkenRun(ctypes.Structure):

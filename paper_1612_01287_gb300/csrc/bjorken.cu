@@ -422,13 +422,9 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
     return set_error(RSLB_ERR_ARG, "rslb_bjorken_init: NULL argument or nruns < 1");
   *out = nullptr;
   if (o->Q_L < 1 || o->Q_L > kBjMaxQL || (o->precision != RSLB_F32 && o->precision != RSLB_F64) ||
-      (o->kp_mode != RSLB_KP_SIMT && o->kp_mode != RSLB_KP_BF16X3 &&
-       o->kp_mode != RSLB_KP_TF32X3) ||
+      (o->kp_mode != RSLB_KP_SIMT && o->kp_mode != RSLB_KP_TF32X3) ||
       !(o->tau0 > 0.0) || !(o->dtau > 0.0) || !std::isfinite(o->dtau))
     return set_error(RSLB_ERR_ARG, "rslb_bjorken_init: invalid options");
-  if (o->kp_mode == RSLB_KP_BF16X3)
-    return set_error(RSLB_ERR_UNSUPPORTED,
-                     "rslb_bjorken_init: RSLB_KP_BF16X3 is not available (use RSLB_KP_TF32X3)");
   if (o->kp_mode == RSLB_KP_TF32X3 && (o->precision != RSLB_F32 || o->Q_L > 4))
     return set_error(RSLB_ERR_UNSUPPORTED,
                      "rslb_bjorken_init: RSLB_KP_TF32X3 needs RSLB_F32 and Q_L <= 4");

@@ -40,6 +40,11 @@ static int noalloc_scratch(void** out) {
                      dev);
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
+    // the large-shared-memory opt-in of the stage kernels holds per device:
+    // make it on this device before its first launch here
+    e = sod_set_attributes();
+    if (e != cudaSuccess)
+      return cuda_error(e, "rslb_sod_step_noalloc: shared-memory opt-in of the stage kernels");
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
@@ -144,6 +149,16 @@ static int noalloc_run(const rslb_config& c, void* f, int nsteps, cudaStream_t s
   if (c.tau_mode == RSLB_TAU_CONST && c.dt >= c.tau)
     return set_error(RSLB_ERR_STIFF, "rslb_sod_step_noalloc: dt >= tau");
 
+  // the tile shape, checked before any device work
+  int dev = 0, max_smem = 0;
+  cudaError_t qe = cudaGetDevice(&dev);
+  if (qe == cudaSuccess)
+    qe = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (qe != cudaSuccess) return cuda_error(qe, "rslb_sod_step_noalloc: device query");
+  const SodLaunch L = sod_pick_launch(sizeof(T) == 8, V, QL, nm, max_smem);
+  if (L.B == 0)
+    return set_error(RSLB_ERR_UNSUPPORTED, "rslb_sod_step_noalloc: V = %d does not fit a tile", V);
+
   void* base = nullptr;
   int rc = noalloc_scratch(&base);
   if (rc) return rc;
@@ -220,14 +235,6 @@ static int noalloc_run(const rslb_config& c, void* f, int nsteps, cudaStream_t s
   tb.gl_w = (const double*)(S + oglw);
   const int nneg = QL * (Qx / 2);
 
-  int dev = 0, max_smem = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  SodLaunch L = sod_pick_launch(sizeof(T) == 8, V, QL, nm, max_smem);
-  if (L.B == 0) {
-    cudaStreamSynchronize(st);
-    return set_error(RSLB_ERR_UNSUPPORTED, "rslb_sod_step_noalloc: V = %d does not fit a tile", V);
-  }
   // caller's populations (pitch Z) into the padded stage buffer
   ok(cudaMemcpy2DAsync(F0, es * ldz, f, es * c.Z, es * c.Z, V, cudaMemcpyDeviceToDevice, st));
   for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {

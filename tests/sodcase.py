@@ -97,3 +97,28 @@ def oracle_rounding_envelope(case, steps, every=16, seed=3):
     e = field_errors(mg, mf)
     e["populations"] = rel_err(g, f)
     return e
+
+
+def oracle_fp32_envelope(case, steps, seed=3):
+    """How far the oracle moves when each of its RK stage values (Eq. rk3) is
+    rounded to FP32 and then nudged by one FP32 ulp (random sign): the size of
+    differences that FP32 storage and arithmetic, about one ulp per stage,
+    produce in this nonlinear scheme over `steps` steps.  The stages are
+    composed here from the oracle's right-hand side L(f) (Eq. L_Sod)."""
+    p = oracle_params(case)
+    f = oracle.sod_init_fields(p, *case["fields"]) if "fields" in case else oracle.sod_init_riemann(p)
+    rng = np.random.default_rng(seed)
+
+    def r32(x):
+        y = x.astype(np.float32)
+        away = np.where(rng.random(y.shape) < 0.5, -np.inf, np.inf).astype(np.float32)
+        return np.nextafter(y, away).astype(np.float64)
+
+    dt = p.dt
+    g = r32(f)
+    for _ in range(steps):
+        g1 = r32(g + dt * oracle.sod_rhs(p, g))
+        g2 = r32(0.75 * g + 0.25 * (g1 + dt * oracle.sod_rhs(p, g1)))
+        g = r32(g / 3.0 + 2.0 / 3.0 * (g2 + dt * oracle.sod_rhs(p, g2)))
+    f = oracle.sod_steps(p, f, steps)
+    return field_errors(oracle.sod_moments(p, g), oracle.sod_moments(p, f))

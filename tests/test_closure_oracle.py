@@ -50,6 +50,36 @@ def test_backprop_full_size_random_subset():
     assert rel < 1e-8, rel
 
 
+def test_forward_by_hand_two_two_two_one():
+    """A 2 -> 2 -> 2 -> 1 network written out scalar by scalar: the flat layout
+    (W1 [H][D] row-major, b1, W2 [H][H], b2, W3 [O][H], b3), W x (not x W) in every
+    layer, SiLU a / (1 + e^-a) after both hidden layers and none after the last."""
+    import math
+    W1 = [[0.5, -1.0], [2.0, 0.25]]
+    b1 = [0.1, -0.3]
+    W2 = [[1.5, -0.5], [0.0, 1.0]]
+    b2 = [-0.2, 0.4]
+    W3 = [[-1.0, 2.0]]
+    b3 = [0.05]
+    theta = np.array([W1[0][0], W1[0][1], W1[1][0], W1[1][1], b1[0], b1[1],
+                      W2[0][0], W2[0][1], W2[1][0], W2[1][1], b2[0], b2[1],
+                      W3[0][0], W3[0][1], b3[0]])
+
+    def silu(a):
+        return a / (1.0 + math.exp(-a))
+
+    for x in ([1.0, 2.0], [-0.7, 0.3]):
+        h1 = [silu(W1[i][0] * x[0] + W1[i][1] * x[1] + b1[i]) for i in range(2)]
+        h2 = [silu(W2[i][0] * h1[0] + W2[i][1] * h1[1] + b2[i]) for i in range(2)]
+        y = W3[0][0] * h2[0] + W3[0][1] * h2[1] + b3[0]
+        got, _ = C.forward(theta, np.array([x]), 2, 2, 1)
+        assert abs(got[0, 0] - y) < 1e-15, (x, got, y)
+    # x = (1, 2) worked on paper: a1 = (-1.4, 2.2), h1 = (-0.276943, 1.980549),
+    # a2 = (-1.605688, 2.380549), h2 = (-0.268452, 2.178993), y = 4.676437
+    y12, _ = C.forward(theta, np.array([[1.0, 2.0]]), 2, 2, 1)
+    assert abs(y12[0, 0] - 4.676437) < 2e-6
+
+
 def test_loss_is_mean_square():
     theta, X, T, D, H, O = small_net()
     y, _ = C.forward(theta, X, D, H, O)

@@ -58,11 +58,18 @@ def test_small_workload_fp32_parity():
     print("fp32 100-step errors", errs)
 
 
-def test_small_workload_full_run_fp32_reported():
-    """FP32 error of the full run (rounding accumulates over 1600 steps with
-    dt/tau = 0.5); reported, and bounded well below the physics."""
-    errs = sodcase.compare(small_case(), 1600, "f32", 1e-3)
-    print("fp32 full-run errors", errs)
+def test_small_workload_full_run_fp32_within_rounding_envelope():
+    """Full run to t = 0.8 in FP32.  FP32 storage and arithmetic perturb every
+    stage by about one FP32 ulp, and the WENO5 weights amplify such
+    perturbations: the oracle, with its stage values rounded to FP32 and nudged
+    by one FP32 ulp at every stage, drifts from itself by ~1e-5 over this run.
+    The GPU must stay within 10 times that envelope."""
+    case = small_case()
+    errs = sodcase.compare(case, 1600, "f32", 1.0, None)
+    env = sodcase.oracle_fp32_envelope(case, 1600)
+    print("fp32 full-run errors", errs, "oracle fp32 envelope", env)
+    for k in sodcase.PARITY_FIELDS:
+        assert errs[k] <= 10.0 * env[k] + TOL32, (k, errs, env)
 
 
 @pytest.mark.parametrize("precision,tol", [("f64", TOL64), ("f32", TOL32)])
@@ -134,6 +141,26 @@ def test_tile_width_does_not_change_results(precision, tiles, tol, Q_xi):
         assert max(errs.values()) <= tol, errs
 
 
+@pytest.mark.parametrize("precision,tol,Q_xi,N_Omega", [
+    ("f64", TOL64, 16, 7), ("f64", TOL64, 16, 10), ("f64", TOL64, 16, 12),
+    ("f32", TOL32, 16, 7), ("f32", TOL32, 16, 10), ("f32", TOL32, 16, 12),
+    ("f32", TOL32, 50, 7), ("f32", TOL32, 50, 12)])
+def test_truncation_orders_above_six(precision, tol, Q_xi, N_Omega):
+    """f^eq truncated above the paper's largest order (App. A stops at m = 6): the
+    a_{l,m} integrals by the 16-node rule (FP32, N_Omega = 7), the 32-node rule
+    (FP64; FP32 above 7) and, at 150 velocities, the packed FP32x2 kernel
+    (N_Omega = 7) or the scalar kernel (N_Omega = 12).  Boosted chambers, so that
+    the high Legendre orders carry weight (Eq. feq_trunc)."""
+    case = dict(Z=72, Q_xi=Q_xi, Q_L=3, N_Omega=N_Omega, bc="fixed_eq", tau=5e-3, dt=1e-3,
+                left=(0.8, 1.2, 0.6), right=(0.3, 0.7, -0.5))
+    if precision == "f32" and Q_xi == 50:
+        from paper_1612_01287_gb300 import Sod
+        with Sod(precision="f32", **sodcase.gpu_kwargs(case)) as s:
+            assert (s.launch_info()[0] == PACKED) == (N_Omega <= 7)
+    errs = sodcase.compare(case, 30, precision, tol, tol if precision == "f64" else None)
+    print(precision, Q_xi, N_Omega, errs)
+
+
 def test_moving_states_negative_beta_fp64():
     """Boosted initial states (sgn(beta) enters f^eq through P_m(sgn(beta) xi))."""
     case = dict(Z=64, Q_xi=16, Q_L=3, N_Omega=6, bc="fixed_eq", tau=5e-3, dt=1e-3,
@@ -141,19 +168,24 @@ def test_moving_states_negative_beta_fp64():
     sodcase.compare(case, 40, "f64", TOL64, TOL64)
 
 
-@pytest.mark.parametrize("precision,tol", [("f64", TOL64), ("f32", TOL32)])
-def test_full_size_sampled_cells(precision, tol):
-    """65536 cells x 600 velocities (the benchmark launch): two steps on the GPU;
+@pytest.mark.parametrize("precision,tol,tau", [("f64", TOL64, 1e-2), ("f32", TOL32, 1e-4),
+                                               ("f32", TOL32, 1e-2), ("f32", TOL32, 1.0),
+                                               ("f32", TOL32, 10.0)])
+def test_full_size_sampled_cells(precision, tol, tau):
+    """65536 cells x 600 velocities (the benchmark launch, every relaxation time of
+    the benchmark in FP32: dt/tau = 0.15 down to 1.5e-6): two steps on the GPU;
     sampled cells are recomputed by the oracle on a window wide enough that its
     own boundaries cannot reach the sample (each RK stage reaches 3 cells)."""
     from paper_1612_01287_gb300 import Sod
-    w = workloads.sod_large(tau=1e-2)
+    w = workloads.sod_large(tau=tau)
     Z, dz = w["Z"], w["dz"]
     xi, _, _, _ = __import__("paper_1612_01287_gb300").quadrature(w["Q_xi"], w["Q_L"])
     dt = w["cfl"] * dz / np.abs(xi).max()
     steps = 2
     with Sod(Z=Z, Q_xi=w["Q_xi"], Q_L=w["Q_L"], N_Omega=w["N_Omega"], bc=w["bc"], tau=w["tau"],
              dt=dt, left=w["left"], right=w["right"], precision=precision) as s:
+        if precision == "f32":
+            assert s.launch_info()[0] == PACKED
         s.step(steps)
         mg = s.moments()
     R = 9 * steps + 6

@@ -153,10 +153,11 @@ def test_aeq_brute_force_integral():
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 30
     for (u, theta) in [(0.3, 0.8), (0.9, 1.2), (2.5, 0.5)]:
-        a = oracle.aeq(1.0, theta, u, 6)
+        a = oracle.aeq(1.0, theta, u, 12)
         u0 = math.sqrt(1 + u * u)
         for l in (0, 1):
-            for m in (0, 2, 5):
+            # up to the largest truncation order the kernels accept (N_Omega = 12)
+            for m in (0, 2, 5, 7, 9, 12):
                 f = lambda c: (u0 - u * c) ** -3 * (1 - theta / (u0 - u * c)) ** l * mp.legendre(m, c)
                 ref = (l + 1) * (l + 2) / (8 * mp.pi) * mp.quad(f, [-1, 0, 1])
                 assert abs(a[l, m] - float(ref)) < 1e-13 * abs(a[0, 0])
@@ -172,7 +173,7 @@ def _mj_moments(n, T, beta):
 
 
 @pytest.mark.parametrize("QL", [2, 3])
-@pytest.mark.parametrize("NO", [2, 5])
+@pytest.mark.parametrize("NO", [2, 5, 12])
 @pytest.mark.parametrize("state", [(1.0, 1.0, 0.0), (0.125, 0.8, 0.6), (0.4, 0.5, -0.9),
                                    (2.0, 1.6, 0.95)])
 def test_truncated_feq_reproduces_mj_moments(QL, NO, state):
@@ -254,6 +255,86 @@ def test_landau_rejects_nonphysical():
         oracle.landau(np.array([1.0, 0.0, -1.0, 0.0, 0.5]))
     with pytest.raises(oracle.OracleError):
         oracle.landau(np.array([-1.0, 0.0, 3.0, 0.0, 1.0]))
+
+
+def _rest_populations(Qx, QL, shape):
+    """Populations w_j w_k/4 [1 + shape(x_k, xi_j)] on scipy's nodes: the rest-frame
+    equilibrium n = T = 1 (Eq. fjk) times a chosen perturbation."""
+    xj, wj = sp.roots_legendre(Qx)
+    xk, wk = sp.roots_genlaguerre(QL, 2)
+    X, XI = np.meshgrid(xk, xj, indexing="ij")  # [k][j], v = k*Qx + j
+    return (np.outer(wk, wj) / 4.0 * (1.0 + shape(X, XI))).ravel()
+
+
+@pytest.mark.parametrize("a", [0.3, -0.45])
+def test_landau_shear_stress_at_rest_closed_form(a):
+    """f = f^eq_rest (1 + a P_2(xi)): by hand, N^t = 1, N^z = T^tz = 0, T^tt = 3,
+    T^zz = (3/2)(2/3 + 4a/15) = 1 + 2a/5 (int xi^2 P_2 = 4/15), so the Landau
+    frame is at rest with n = 1, E = 3, P = T = 1, and Pi = T^zz - P = 2a/5
+    (Eq. pi_val with T^tt = E), q = 0 (Eq. q_val with N^z = 0)."""
+    Qx, QL = 6, 3
+    f = _rest_populations(Qx, QL, lambda x, xi: a * 0.5 * (3 * xi**2 - 1))
+    L = oracle.landau(oracle.moments(Qx, QL, f))
+    assert abs(L["Pi"] - 0.4 * a) < 1e-14
+    assert abs(L["q"]) < 1e-14
+    assert abs(L["beta"]) < 1e-15
+    for k, v in (("n", 1.0), ("E", 3.0), ("P", 1.0), ("T", 1.0), ("gamma", 1.0)):
+        assert abs(L[k] - v) < 1e-14, (k, L[k])
+
+
+@pytest.mark.parametrize("b", [0.2, -0.35])
+def test_landau_heat_flux_at_rest_closed_form(b):
+    """f = f^eq_rest (1 + b (x - 4) xi): the radial factor makes T^tz vanish
+    (int e^-x x^3 (x - 4) = 24 - 24 = 0), so beta = 0, while
+    N^z = (b/4)(int e^-x x^2 (x - 4))(2/3) = (b/4)(-2)(2/3) = -b/3.  With n = T = 1,
+    q = -4T(N^z - n beta gamma) = 4b/3 and Pi = 0 (T^tt = 3, T^zz = 1)."""
+    Qx, QL = 6, 3
+    f = _rest_populations(Qx, QL, lambda x, xi: b * (x - 4.0) * xi)
+    M = oracle.moments(Qx, QL, f)
+    assert abs(M[3]) < 1e-14 and abs(M[1] + b / 3.0) < 1e-14
+    L = oracle.landau(M)
+    assert abs(L["q"] - 4.0 * b / 3.0) < 1e-14
+    assert abs(L["Pi"]) < 1e-14
+    assert abs(L["beta"]) < 1e-15
+    assert abs(L["n"] - 1.0) < 1e-14 and abs(L["T"] - 1.0) < 1e-14
+
+
+def _boost(M, v):
+    """Moments (N^t, N^z, T^tt, T^tz, T^zz) seen from a frame moving with velocity v
+    along z: N' = Lambda N, T' = Lambda T Lambda^T."""
+    g = 1.0 / math.sqrt(1.0 - v * v)
+    Lm = np.array([[g, -g * v], [-g * v, g]])
+    N = Lm @ np.array([M[0], M[1]])
+    T = Lm @ np.array([[M[2], M[3]], [M[3], M[4]]]) @ Lm.T
+    return np.array([N[0], N[1], T[0, 0], T[0, 1], T[1, 1]])
+
+
+@pytest.mark.parametrize("v", [0.3, -0.7, 0.9])
+def test_landau_lorentz_covariance_off_equilibrium(v):
+    """An anisotropic, heat-conducting state with q and Pi far from zero, seen from a
+    boosted frame.  n, E, P, T and Pi are Lorentz scalars (Pi^{ab} = Pi (z^a z^b -
+    transverse/2) with the unit vector z = gamma(beta, 0, 0, 1)); q^a = q (beta, 0, 0, 1)
+    = (q/gamma) z^a, so q/gamma is the invariant; beta adds relativistically.  The
+    printed heat flux must also satisfy q^a = -4T (N^a - n u^a) in its time component
+    (Eq. qL with E + P = 4nT), which Eq. q_val does not use, and n = u_a N^a."""
+    Qx, QL = 10, 3
+    f = _rest_populations(Qx, QL, lambda x, xi: 0.3 * 0.5 * (3 * xi**2 - 1) +
+                          0.2 * (x - 4.0) * xi + 0.1 * xi)
+    M = oracle.moments(Qx, QL, f)
+    L0 = oracle.landau(M)
+    assert abs(L0["Pi"]) > 0.05 and abs(L0["q"]) > 0.05 and abs(L0["beta"]) > 1e-3
+    for ref in (L0, oracle.landau(_boost(M, v))):
+        Mr = M if ref is L0 else _boost(M, v)
+        g, b, n, T = ref["gamma"], ref["beta"], ref["n"], ref["T"]
+        assert abs(ref["q"] * b + 4.0 * T * (Mr[0] - n * g)) < 1e-13
+        assert abs(n - g * (Mr[0] - b * Mr[1])) < 1e-13
+    L1 = oracle.landau(_boost(M, v))
+    for k in ("n", "E", "P", "T"):
+        assert abs(L1[k] / L0[k] - 1.0) < 1e-13, (k, L0[k], L1[k])
+    assert abs(L1["Pi"] - L0["Pi"]) < 1e-13 * L0["E"]
+    assert abs(L1["q"] / L1["gamma"] - L0["q"] / L0["gamma"]) < 1e-13 * L0["E"]
+    b0 = L0["beta"]
+    assert abs(L1["beta"] - (b0 - v) / (1.0 - b0 * v)) < 1e-14
 
 
 # -------------------------------------------------------------- WENO5

@@ -13,6 +13,12 @@ CASES = [
     ("f32", dict(Z=200, Q_xi=20, Q_L=3, N_Omega=5, bc="outflow", tau=1e-3, dt=5e-4), 1e-6),
     ("f64", dict(Z=150, Q_xi=7, Q_L=2, N_Omega=3, bc="fixed_eq", tau=2e-3, dt=1e-3,
                  z_min=-0.5, z_max=0.5, right=(0.125, 0.5, 0.0)), 1e-12),
+    # 150 velocities: the packed FP32x2 stage kernel, whose bulk-tensor maps then
+    # point into the static array
+    ("f32", dict(Z=130, Q_xi=50, Q_L=3, N_Omega=5, bc="outflow", tau=5e-3, dt=1e-3), 1e-6),
+    # periodic domain with the eta/s relaxation-time law, packed kernel
+    ("f32", dict(Z=96, Q_xi=50, Q_L=3, N_Omega=5, bc="periodic", tau_mode="etas", tau_AW0=4e-3,
+                 lambda_ref=1.0, dt=1e-3), 1e-6),
 ]
 
 
