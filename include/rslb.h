@@ -122,7 +122,18 @@ typedef struct rslb_config {
    * N_Omega <= 7), 128, 64, 32 or 16 (RSLB_F32), 16 or
    * 8 (RSLB_F64).  A tuning knob; results agree to rounding. */
   int tile_cells;
+  /* Form of the packed FP32x2 kernel: RSLB_PACKED_AUTO (the persistent
+   * pipelined form where it fits), RSLB_PACKED_PER_TILE (one CTA per tile)
+   * or RSLB_PACKED_PERSISTENT (one CTA per SM walking the tiles with two
+   * tile buffers; RSLB_ERR_ARG where it does not fit: it needs V <= ~700,
+   * Z >= RSLB_PACKED_TILE_CELLS + 8).  Both forms give bitwise identical
+   * results. */
+  int packed_form;
 } rslb_config;
+
+#define RSLB_PACKED_AUTO 0
+#define RSLB_PACKED_PER_TILE 1
+#define RSLB_PACKED_PERSISTENT 2
 
 typedef struct rslb_handle rslb_handle;
 
@@ -184,8 +195,9 @@ int rslb_set_state(rslb_handle* h, const void* f, int on_device);
 int rslb_time(const rslb_handle* h, double* t, long long* steps);
 
 /* The stage kernel the handle launches: cells per CTA tile
- * (RSLB_PACKED_TILE_CELLS = packed
- * FP32x2 kernel) and threads per CTA.  Errors: RSLB_ERR_ARG. */
+ * (RSLB_PACKED_TILE_CELLS = packed FP32x2 kernel) and threads per CTA (the
+ * persistent pipelined form of the packed kernel has more threads than
+ * 8 * RSLB_PACKED_TILE_CELLS).  Errors: RSLB_ERR_ARG. */
 int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* threads);
 
 /*
@@ -202,8 +214,8 @@ int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* threads);
  * array of RSLB_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the
  * library holds until the process exits.
  *
- *   cfg:    the configuration, as for rslb_init (n0/T0/beta0 and tile_cells
- *           are ignored; the populations come from f);
+ *   cfg:    the configuration, as for rslb_init (n0/T0/beta0, tile_cells and
+ *           packed_form are ignored; the populations come from f);
  *   f:      caller-owned device array of V*Z values in the cfg precision
  *           (f[v*Z + s], v = k*Q_xi + j), advanced in place by nsteps steps,
  *           the same TVD-RK3 steps as rslb_step performs;

@@ -39,7 +39,10 @@ class Config(ctypes.Structure):
                 ("nL", ctypes.c_double), ("TL", ctypes.c_double), ("betaL", ctypes.c_double),
                 ("nR", ctypes.c_double), ("TR", ctypes.c_double), ("betaR", ctypes.c_double),
                 ("n0", ctypes.c_void_p), ("T0", ctypes.c_void_p), ("beta0", ctypes.c_void_p),
-                ("tile_cells", ctypes.c_int)]
+                ("tile_cells", ctypes.c_int), ("packed_form", ctypes.c_int)]
+
+
+PACKED_FORMS = {"auto": 0, "per_tile": 1, "persistent": 2}
 
 
 _lib = None
@@ -113,7 +116,7 @@ class Sod:
     def __init__(self, Z, Q_xi, Q_L=3, N_Omega=None, z_min=-1.0, z_max=1.0, precision="f32",
                  bc="outflow", tau_mode="const", tau=1e-3, tau_AW0=0.0, lambda_ref=1.0, dt=5e-4,
                  left=(1.0, 1.0, 0.0), right=(0.125, 0.8, 0.0), fields=None, stream=None,
-                 tile_cells=0):
+                 tile_cells=0, packed_form="auto"):
         """left/right: (n, T, beta); fields: optional (n0, T0, beta0) arrays of length Z."""
         if N_Omega is None:
             N_Omega = min(Q_xi - 1, 5)
@@ -128,7 +131,8 @@ class Sod:
                      F64 if self.fp64 else F32, BC[bc] if isinstance(bc, str) else int(bc),
                      TAU[tau_mode] if isinstance(tau_mode, str) else int(tau_mode),
                      tau, tau_AW0, lambda_ref, dt, left[0], left[1], left[2],
-                     right[0], right[1], right[2], None, None, None, int(tile_cells))
+                     right[0], right[1], right[2], None, None, None, int(tile_cells),
+                     PACKED_FORMS[packed_form])
         if fields is not None:
             arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in fields]
             self._keep = arrs
@@ -224,7 +228,7 @@ def sod_step_noalloc(f_ptr, nsteps, Z, Q_xi, Q_L=3, N_Omega=None, z_min=-1.0, z_
                  BC[bc] if isinstance(bc, str) else int(bc),
                  TAU[tau_mode] if isinstance(tau_mode, str) else int(tau_mode),
                  tau, tau_AW0, lambda_ref, dt, left[0], left[1], left[2],
-                 right[0], right[1], right[2], None, None, None, 0)
+                 right[0], right[1], right[2], None, None, None, 0, 0)
     _check(fn(ctypes.byref(cfg), ctypes.c_void_p(f_ptr), int(nsteps), _stream_ptr(stream)))
 
 

@@ -364,6 +364,32 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
   }
   if (L.B == 0)
     return set_error(RSLB_ERR_UNSUPPORTED, "rslb_init: V = %d velocities do not fit one tile", V);
+  if (c.packed_form < RSLB_PACKED_AUTO || c.packed_form > RSLB_PACKED_PERSISTENT)
+    return set_error(RSLB_ERR_ARG, "rslb_init: unknown packed_form %d", c.packed_form);
+  if (L.B == kSod32Cells && c.packed_form != RSLB_PACKED_PER_TILE) {
+    // the persistent pipelined form where it fits (the population buffers are
+    // cudaMalloc'd, so 16-byte aligned for its bulk-tensor copies)
+    SodGeom gq;
+    std::memset(&gq, 0, sizeof(gq));
+    gq.Z = c.Z;
+    gq.ldz = (c.Z + 31) / 32 * 32;
+    gq.V = V;
+    gq.QL = QL;
+    gq.nm = nm;
+    int nsm = 0;
+    ce = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) return cuda_error(ce, "rslb_init: SM count");
+    if (sod32p_fits(gq, max_smem)) {
+      L.form = 1;
+      L.nsm = nsm;
+    } else if (c.packed_form == RSLB_PACKED_PERSISTENT) {
+      return set_error(RSLB_ERR_ARG,
+                       "rslb_init: the persistent packed kernel does not fit (V = %d, Z = %d)", V,
+                       c.Z);
+    }
+  } else if (c.packed_form == RSLB_PACKED_PERSISTENT) {
+    return set_error(RSLB_ERR_ARG, "rslb_init: packed_form needs the packed FP32 kernel");
+  }
 
   rslb_handle* h = new rslb_handle();
   std::memset((void*)h, 0, sizeof(*h));
@@ -687,7 +713,9 @@ extern "C" int rslb_launch_info(const rslb_handle* h, int* tile_cells, int* thre
   clear_error();
   if (!h) return set_error(RSLB_ERR_ARG, "rslb_launch_info: NULL handle");
   if (tile_cells) *tile_cells = h->launch.B;
-  if (threads) *threads = h->launch.B == kSod32Cells ? kSod32Threads : 320;
+  if (threads)
+    *threads = h->launch.B == kSod32Cells ? (h->launch.form == 1 ? sod32p_threads() : kSod32Threads)
+                                          : 320;
   return RSLB_OK;
 }
 

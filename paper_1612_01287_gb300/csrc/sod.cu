@@ -653,7 +653,9 @@ cudaError_t sod_set_attributes() {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
   }
-  return sod32_set_attributes();
+  cudaError_t e = sod32_set_attributes();
+  if (e != cudaSuccess) return e;
+  return sod32p_set_attributes();
 }
 
 SodLaunch sod_pick_launch(bool fp64, int V, int QL, int nm, int max_smem) {
@@ -709,6 +711,8 @@ cudaError_t sod_stage_launch(const SodLaunch& L, const SodGeom& g, const SodTabl
                              const int* rowv, int nneg, const T* fin, const T* fn, T* fout,
                              int stage, int* err, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
+    if (L.B == kSod32Cells && L.form == 1)
+      return sod32p_stage_launch(g, tb, rowv, nneg, fin, fn, fout, stage, err, L.nsm, st);
     if (L.B == kSod32Cells) return sod32_stage_launch(g, tb, rowv, nneg, fin, fn, fout, stage, err, st);
   }
   switch (L.B) {

@@ -72,6 +72,8 @@ struct SodTablesF64 {
 struct SodLaunch {
   int B;        // cells per CTA
   size_t smem;  // dynamic shared memory bytes
+  int form;     // packed FP32 kernel: 0 = one CTA per tile, 1 = persistent pipelined
+  int nsm;      // SMs of the device (persistent grid)
 };
 
 // Opt the stage kernels into large dynamic shared memory (call at set-up,
@@ -108,6 +110,16 @@ size_t sod32_smem_bytes(int V, int QL);
 cudaError_t sod32_stage_launch(const SodGeom& g, const SodTables<float>& tb, const int* rowv,
                                int nneg, const float* fin, const float* fn, float* fout, int stage,
                                int* err, cudaStream_t st);
+
+// Persistent pipelined form of the packed FP32x2 kernel (sod32p.cu): one CTA
+// per SM, two tile buffers, warp-specialised producer / cell / sweep groups.
+size_t sod32p_smem_bytes(int V, int QL);
+int sod32p_threads();
+cudaError_t sod32p_set_attributes();
+bool sod32p_fits(const SodGeom& g, int max_smem);
+cudaError_t sod32p_stage_launch(const SodGeom& g, const SodTables<float>& tb, const int* rowv,
+                                int nneg, const float* fin, const float* fn, float* fout,
+                                int stage, int* err, int num_sms, cudaStream_t st);
 
 // Batched stage launches: a persistent grid of `grid` CTAs walks the task list
 // (tile width B as chosen by sod_pick_launch / the tuner for this class).

@@ -299,6 +299,46 @@ def test_boundary_tiles_at_many_velocities(bc, precision, tol):
     print(bc, precision, errs)
 
 
+@pytest.mark.parametrize("Z,Q_xi,bc,tau_mode", [
+    (36, 200, "outflow", "const"),      # two tiles, the second ragged
+    (100, 200, "fixed_eq", "const"),    # ragged last tile, fixed ghosts
+    (300, 200, "periodic", "etas"),     # periodic ghosts, eta/s law
+    (130, 200, "outflow", "none"),      # collisionless
+    (1000, 200, "outflow", "const"),    # several tiles per CTA at this grid
+    (140, 50, "fixed_eq", "const"),     # 150 velocities: one sweep round
+    (200, 180, "outflow", "etas"),      # 540 velocities, uneven rounds
+])
+def test_persistent_packed_kernel_is_bitwise_the_per_tile_kernel(Z, Q_xi, bc, tau_mode):
+    """The persistent pipelined form of the packed FP32x2 kernel (one CTA per SM,
+    two tile buffers, bulk-tensor staging of every tile including the boundary
+    ones, ghost cells filled afterwards) runs the same phase code as the
+    one-CTA-per-tile form: the populations agree bitwise after 13 steps."""
+    from paper_1612_01287_gb300 import Sod
+    n, T, b = workloads.random_smooth_fields(Z, beta_max=0.5)
+    case = dict(Z=Z, Q_xi=Q_xi, Q_L=3, N_Omega=5, bc=bc, tau_mode=tau_mode, tau=5e-3,
+                tau_AW0=4e-3, lambda_ref=1.0, dt=1e-3, fields=(n, T, b))
+    out = {}
+    for form in ("per_tile", "persistent"):
+        with Sod(precision="f32", packed_form=form, **case) as s:
+            tc, nt = s.launch_info()
+            assert tc == PACKED
+            s.step(13)
+            out[form] = (nt, s.get_state())
+    assert out["persistent"][0] != out["per_tile"][0]
+    np.testing.assert_array_equal(out["persistent"][1], out["per_tile"][1])
+
+
+def test_persistent_packed_kernel_is_the_default_where_it_fits():
+    from paper_1612_01287_gb300 import RslbError, Sod
+    case = dict(Q_xi=200, Q_L=3, N_Omega=5, bc="outflow", tau=1e-2, dt=1e-4)
+    with Sod(Z=64, precision="f32", **case) as s:
+        assert s.launch_info() == (PACKED, 512)
+    with Sod(Z=30, precision="f32", **case) as s:  # too short for its bulk copies
+        assert s.launch_info() == (PACKED, 8 * PACKED)
+    with pytest.raises(RslbError):
+        Sod(Z=30, precision="f32", packed_form="persistent", **case)
+
+
 @pytest.mark.parametrize("precision,tol", [("f64", 1e-13), ("f32", 1e-12)])
 @pytest.mark.parametrize("Z,Q_xi", [(1000, 50), (77, 7)])
 def test_output_moments_of_a_given_state(precision, tol, Z, Q_xi):
