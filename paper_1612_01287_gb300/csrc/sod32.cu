@@ -28,8 +28,8 @@ constexpr int kMinCtas = kB2 <= 20 ? 3 : 2;  // CTAs per SM the registers are si
 
 // Shared memory: tile [rows][kP] floats (rows = V rounded up to whole TMA
 // boxes), then partial moments, cell scalars, coefficients
-// [QL][kH][kMP][2] floats, gco [kH][4] floats, an mbarrier and the five
-// moment weights of every velocity [5][V].
+// [QL][kH][kMP][2] floats, gco [kH][4] floats, an mbarrier, the five
+// moment weights of every velocity [5][V] and the coefficient constants.
 static size_t tile_rows(int V) {
   int nb = 0;
   const int r = tma_box_rows(V, &nb);
@@ -40,7 +40,8 @@ size_t sod32_smem_bytes(int V, int QL) {
   auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
   return al(sizeof(float) * tile_rows(V) * kP) + al(sizeof(double) * 5 * kB2) +
          al(sizeof(double) * 8 * kB2) + al(sizeof(float) * (size_t)QL * kH * kMP * 2) +
-         al(sizeof(float) * kH * 4) + 128 + al(sizeof(float) * 5 * (size_t)V) + 128;
+         al(sizeof(float) * kH * 4) + 128 + al(sizeof(float) * 5 * (size_t)V) +
+         al(sizeof(float) * kConsts) + 128;
 }
 
 // One stage of one tile starting at cell s0 (the whole CTA).
@@ -65,8 +66,11 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
   uint64_t* bar = reinterpret_cast<uint64_t*>(
       reinterpret_cast<unsigned char*>(gco) + al(sizeof(float) * kH * 4));
   float* mws = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bar) + 128);
+  float* cst = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(mws) +
+                                        al(sizeof(float) * 5 * (size_t)V));
   auto copy_weights = [&]() {
     for (int e = threadIdx.x; e < 5 * V; e += kNT) mws[e] = tb.mw[e];
+    load_consts(cst, tb, g.QL, threadIdx.x, kNT);
   };
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -134,7 +138,7 @@ __device__ __forceinline__ void sod32_tile(const float* __restrict__ fin,
     if (tid < kB2) landau_cell(msum, cellf, gco, g, s0, tid, err);
     __syncthreads();
     // ---- 3b. f^eq coefficients: 8 threads per cell share the 16 nodes ----
-    coefs(cellf, coef, g, tb, tid);
+    coefs(cellf, coef, g, cst, tid);
     __syncthreads();
   } else {
     for (int i = tid; i < g.QL * kH * kMP * 2 + kH * 4; i += kNT) coef[i] = 0.f;

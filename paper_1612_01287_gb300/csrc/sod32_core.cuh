@@ -419,10 +419,25 @@ __device__ __forceinline__ void landau_cell(const double* msum, float* cellf, fl
   gco[4 * i + 2 + h] = g1;
 }
 
+// FP32 constants of the coefficient phase, copied into shared memory by
+// load_consts: cst[0..15] the nodes and cst[16..31] the weights of the 16-node
+// Gauss-Legendre rule of the a_{l,m} integrals, cst[32 + k] = L_1^{(2)}(x_k).
+constexpr int kConsts = 32 + 8;
+
+__device__ __forceinline__ void load_consts(float* cst, const SodTables<float>& tb, int QL, int t,
+                                            int nt) {
+  for (int e = t; e < 32 + QL; e += nt)
+    cst[e] = e < 16 ? float(tb.gl_t[kAeqNodes + e])
+                    : (e < 32 ? float(tb.gl_w[kAeqNodes + e - 16]) : tb.L1k[e - 32]);
+}
+
 // f^eq coefficients of the tile: thread t (0 <= t < 8 kB2), 8 threads per cell
-// share the 16 nodes of the a_{l,m} rule; coef [QL][kH][kMP][2 halves].
+// share the 16 nodes of the a_{l,m} rule; after an xor butterfly every thread
+// of a cell holds all the integrals, and thread q writes the coefficients of
+// order m = q for every radial node; coef [QL][kH][kMP][2 halves].
 __device__ __forceinline__ void coefs(const float* cellf, float* coef, const SodGeom& g,
-                                      const SodTables<float>& tb, int t) {
+                                      const float* cst, int t) {
+  static_assert(kMP == 8, "one thread per order m");
   const int c = t >> 3, q = t & 7;  // 8 threads per cell
   const float ud = cellf[2 * kB2 + c];
   const float A = cellf[3 * kB2 + c], sh2 = cellf[5 * kB2 + c];
@@ -433,8 +448,7 @@ __device__ __forceinline__ void coefs(const float* cellf, float* coef, const Sod
   for (int m = 0; m < kMaxM; ++m) { J3[m] = 0.f; J4[m] = 0.f; }
 #pragma unroll
   for (int i = 0; i < kAeqNodesF32 / 8; ++i)  // the 16-node rule (N_Omega <= 7 here)
-    aeq_node<float>(float(tb.gl_t[kAeqNodes + q + 8 * i]), float(tb.gl_w[kAeqNodes + q + 8 * i]),
-                    A, sh2, uinv, at_rest, g.nm, J3, J4);
+    aeq_node<float>(cst[q + 8 * i], cst[16 + q + 8 * i], A, sh2, uinv, at_rest, g.nm, J3, J4);
 #pragma unroll
   for (int o = 4; o >= 1; o >>= 1)
 #pragma unroll
@@ -443,25 +457,24 @@ __device__ __forceinline__ void coefs(const float* cellf, float* coef, const Sod
         J3[m] += __shfl_xor_sync(0xffffffffu, J3[m], o);
         J4[m] += __shfl_xor_sync(0xffffffffu, J4[m], o);
       }
-  if (q == 0) {
-    const float fac = cellf[7 * kB2 + c] * cellf[0 * kB2 + c] * cellf[4 * kB2 + c] * 0.25f;
-    const float theta = cellf[1 * kB2 + c];
-    const float sgn = cellf[6 * kB2 + c];
-    const int h = c / kH, i = c - h * kH;
-    float sm = fac;
+  const int m = q;
+  float j3 = 0.f, j4 = 0.f;
 #pragma unroll
-    for (int m = 0; m < kMP; ++m) {
-      if (m < g.nm) {
-        const float hh = sm * float(0.5 * (2 * m + 1));
-        const float d = J3[m] - theta * J4[m];
-        for (int k = 0; k < g.QL; ++k)
-          coef[(((size_t)k * kH + i) * kMP + m) * 2 + h] = hh * (J3[m] + tb.L1k[k] * d);
-        sm *= sgn;
-      } else {
-        for (int k = 0; k < g.QL; ++k) coef[(((size_t)k * kH + i) * kMP + m) * 2 + h] = 0.f;
-      }
+  for (int mm = 0; mm < kMP; ++mm)
+    if (mm == m) {
+      j3 = J3[mm];
+      j4 = J4[mm];
     }
-  }
+  const float fac = cellf[7 * kB2 + c] * cellf[0 * kB2 + c] * cellf[4 * kB2 + c] * 0.25f;
+  const float theta = cellf[1 * kB2 + c];
+  const float sgn = cellf[6 * kB2 + c];
+  const int h = c / kH, i = c - h * kH;
+  const float sm = ((m & 1) && sgn < 0.f) ? -fac : fac;  // fac sgn^m (sgn = +-1)
+  const float hh = sm * (float(m) + 0.5f);                // (2m + 1)/2, exact
+  const float d = j3 - theta * j4;
+  for (int k = 0; k < g.QL; ++k)
+    coef[(((size_t)k * kH + i) * kMP + m) * 2 + h] =
+        m < g.nm ? hh * (j3 + cst[32 + k] * d) : 0.f;
 }
 
 // Row sweeps: rows ir = first, first + stride, ... (negative-xi rows first,
@@ -485,20 +498,63 @@ __device__ __forceinline__ void sweep_rows(float* tile, const float* coef, const
   }
 }
 
+// Per-row tables of the sweep in row order (shared memory): velocity index,
+// xi, radial index and w_j w_k P_m(xi_j) [kMP][V]; the same values as the
+// tables sweep_rows reads from global memory.
+struct RowTables {
+  int* v;
+  float* xi;
+  int* k;
+  float* wp;
+};
+
+__device__ __forceinline__ void load_row_tables(const RowTables& rt, const SodGeom& g,
+                                                const SodTables<float>& tb,
+                                                const int* __restrict__ rowv, int t, int nt) {
+  const int V = g.V;
+  for (int ir = t; ir < V; ir += nt) {
+    const int v = rowv[ir];
+    rt.v[ir] = v;
+    rt.xi[ir] = tb.xi[v];
+    rt.k[ir] = tb.kidx[v];
+#pragma unroll
+    for (int m = 0; m < kMP; ++m) rt.wp[m * V + ir] = (m < g.nm) ? tb.wp[m * V + v] : 0.f;
+  }
+}
+
+__device__ __forceinline__ void sweep_rows_tab(float* tile, const float* coef, const float* gco,
+                                               const SodGeom& g, const RowTables& rt, int nneg,
+                                               int first, int stride) {
+  const float inv_dz = float(g.inv_dz), dt = float(g.dt);
+  const int V = g.V;
+  for (int ir = first; ir < V; ir += stride) {
+    const int v = rt.v[ir];
+    const float xi = rt.xi[ir];
+    const int k = rt.k[ir];
+    float2 wp2[kMP];
+#pragma unroll
+    for (int m = 0; m < kMP; ++m) wp2[m] = splat(rt.wp[m * V + ir]);
+    const float* ck = coef + (size_t)k * kH * kMP * 2;
+    if (ir >= nneg) sweep_row2<true>(tile + v * kP, xi, wp2, g.nm, ck, gco, inv_dz, dt);
+    else sweep_row2<false>(tile + v * kP, xi, wp2, g.nm, ck, gco, inv_dz, dt);
+  }
+}
+
 // Store: cell c of the tile is position 4 + c; stages 2 and 3 combine with
 // f_n (Eq. rk3: 3/4 f_n + 1/4 f, then 1/3 f_n + 2/3 f).  Threads t of nt.
+template <int INFL = kInflight>
 __device__ __forceinline__ void store(const float* tile, const float* __restrict__ fn, float* fout,
                                       const SodGeom& g, int stage, int s0, int t, int nt) {
   const int V = g.V;
   const float a = (stage == 1) ? 0.75f : 1.f / 3.f;
   const float b = (stage == 1) ? 0.25f : 2.f / 3.f;
   if (s0 + kB2 <= g.Z) {
-    // full tile: kB2/4 chunks of 4 cells per row, 16-byte accesses, eight loads
+    // full tile: kB2/4 chunks of 4 cells per row, 16-byte accesses, INFL loads
     // of f_n in flight per thread
-    for (int base_i = t; base_i < V * (kB2 / 4); base_i += kInflight * nt) {
-      float4 fo[kInflight];
+    for (int base_i = t; base_i < V * (kB2 / 4); base_i += INFL * nt) {
+      float4 fo[INFL];
 #pragma unroll
-      for (int u = 0; u < kInflight; ++u) {
+      for (int u = 0; u < INFL; ++u) {
         const int idx = base_i + u * nt;
         if (stage != 0 && idx < V * (kB2 / 4)) {
           const int v = idx / (kB2 / 4), q = idx - v * (kB2 / 4);
@@ -506,7 +562,7 @@ __device__ __forceinline__ void store(const float* tile, const float* __restrict
         }
       }
 #pragma unroll
-      for (int u = 0; u < kInflight; ++u) {
+      for (int u = 0; u < INFL; ++u) {
         const int idx = base_i + u * nt;
         if (idx < V * (kB2 / 4)) {
           const int v = idx / (kB2 / 4), q = idx - v * (kB2 / 4);

@@ -39,6 +39,7 @@ constexpr int kCellT = 32 * kCellWarps;    // 128
 constexpr int kSweepT = 32 * kSweepWarps;  // 384
 constexpr int kThreads = kCellT + kSweepT;
 constexpr int kCellGroups = kB2 / 4;  // moments: 4 cells per warp pass
+constexpr int kStoreInflight = 12;    // f_n loads in flight per sweep thread in the store
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at the maximum SM clock
 constexpr uint32_t kSuspendNs = 1000;
 constexpr int kBarCell = 1, kBarSweep = 2;  // named barriers (0 is __syncthreads)
@@ -101,6 +102,8 @@ struct Smem {
   float* coef[2];
   float* gco[2];
   float* mws;
+  float* cst;
+  RowTables rt;
   double* msum;
   float* cellf;
   uint64_t* full;
@@ -120,10 +123,15 @@ __host__ __device__ __forceinline__ size_t coef_bytes(int QL) {
   return al128(sizeof(float) * (size_t)QL * kH * kMP * 2);
 }
 
+__host__ __device__ __forceinline__ size_t rowtab_bytes(int V) {
+  return 3 * al128(sizeof(int) * (size_t)V) + al128(sizeof(float) * kMP * (size_t)V);
+}
+
 __host__ __device__ __forceinline__ size_t smem_total(int V, int QL) {
   return 2 * tile_bytes(V) + 2 * coef_bytes(QL) + 2 * al128(sizeof(float) * kH * 4) +
-         al128(sizeof(float) * 5 * (size_t)V) + al128(sizeof(double) * 5 * kB2) +
-         al128(sizeof(float) * 8 * kB2) + 128 + 128;
+         al128(sizeof(float) * 5 * (size_t)V) + al128(sizeof(float) * kConsts) +
+         rowtab_bytes(V) + al128(sizeof(double) * 5 * kB2) + al128(sizeof(float) * 8 * kB2) +
+         128 + 128;
 }
 
 __device__ __forceinline__ Smem carve(unsigned char* base, int V, int QL) {
@@ -143,6 +151,16 @@ __device__ __forceinline__ Smem carve(unsigned char* base, int V, int QL) {
   }
   m.mws = reinterpret_cast<float*>(base + o);
   o += al128(sizeof(float) * 5 * (size_t)V);
+  m.cst = reinterpret_cast<float*>(base + o);
+  o += al128(sizeof(float) * kConsts);
+  m.rt.v = reinterpret_cast<int*>(base + o);
+  o += al128(sizeof(int) * (size_t)V);
+  m.rt.xi = reinterpret_cast<float*>(base + o);
+  o += al128(sizeof(float) * (size_t)V);
+  m.rt.k = reinterpret_cast<int*>(base + o);
+  o += al128(sizeof(int) * (size_t)V);
+  m.rt.wp = reinterpret_cast<float*>(base + o);
+  o += al128(sizeof(float) * kMP * (size_t)V);
   m.msum = reinterpret_cast<double*>(base + o);
   o += al128(sizeof(double) * 5 * kB2);
   m.cellf = reinterpret_cast<float*>(base + o);
@@ -213,6 +231,8 @@ sod32p_stage_kernel(const float* __restrict__ fin, const float* __restrict__ fn,
   if (tid == issuer)
     for (; issued < 2 && issued < ntile_cta; ++issued) issue(issued);
   for (int e = tid; e < 5 * V; e += kThreads) S.mws[e] = tb.mw[e];
+  load_consts(S.cst, tb, g.QL, tid, kThreads);
+  load_row_tables(S.rt, g, tb, rowv, tid, kThreads);
   __syncthreads();
 
   const bool collide = g.tau_mode != kTauNone;
@@ -239,11 +259,15 @@ sod32p_stage_kernel(const float* __restrict__ fin, const float* __restrict__ fn,
         for (int grp = warp; grp < kCellGroups; grp += kCellWarps)
           moments(tile, S.mws, S.msum, V, grp, lane);
         named_sync(kBarCell, kCellT);
-        // Landau matching: 7 cells per warp, one warp per SM sub-partition
-        if (lane < kB2 / kCellWarps)
-          landau_cell(S.msum, S.cellf, S.gco[b], g, s0, warp + kCellWarps * lane, err);
+        // Landau matching: the cells spread over the warps, so that the FP64
+        // work of the tile is shared by all four SM sub-partitions
+        {
+          const int c = warp + kCellWarps * lane;
+          if (lane < (kB2 + kCellWarps - 1) / kCellWarps && c < kB2)
+            landau_cell(S.msum, S.cellf, S.gco[b], g, s0, c, err);
+        }
         named_sync(kBarCell, kCellT);
-        for (int q = tid; q < kCellThreads; q += kCellT) coefs(S.cellf, S.coef[b], g, tb, q);
+        for (int q = tid; q < kCellThreads; q += kCellT) coefs(S.cellf, S.coef[b], g, S.cst, q);
       } else {
         for (int e = tid; e < g.QL * kH * kMP * 2; e += kCellT) S.coef[b][e] = 0.f;
         for (int e = tid; e < kH * 4; e += kCellT) S.gco[b][e] = 0.f;
@@ -269,9 +293,9 @@ sod32p_stage_kernel(const float* __restrict__ fin, const float* __restrict__ fn,
       break;
     }
     float* tile = S.tile[b];
-    sweep_rows(tile, S.coef[b], S.gco[b], g, tb, rowv, nneg, st, kSweepT);
+    sweep_rows_tab(tile, S.coef[b], S.gco[b], g, S.rt, nneg, st, kSweepT);
     named_sync(kBarSweep, kSweepT);
-    store(tile, fn, fout, g, stage, s0, st, kSweepT);
+    store<kStoreInflight>(tile, fn, fout, g, stage, s0, st, kSweepT);
     // every sweep thread is done with this buffer before the next copy
     // (async proxy) overwrites it
     fence_proxy_async();
