@@ -122,12 +122,12 @@ typedef struct rslb_config {
    * N_Omega <= 7), 128, 64, 32 or 16 (RSLB_F32), 16 or
    * 8 (RSLB_F64).  A tuning knob; results agree to rounding. */
   int tile_cells;
-  /* Form of the packed FP32x2 kernel: RSLB_PACKED_AUTO (the persistent
-   * pipelined form where it fits), RSLB_PACKED_PER_TILE (one CTA per tile)
-   * or RSLB_PACKED_PERSISTENT (one CTA per SM walking the tiles with two
-   * tile buffers; RSLB_ERR_ARG where it does not fit: it needs V <= ~700,
-   * Z >= RSLB_PACKED_TILE_CELLS + 8).  Both forms give bitwise identical
-   * results. */
+  /* Form of the packed FP32x2 kernel: RSLB_PACKED_AUTO or
+   * RSLB_PACKED_PER_TILE (one CTA per tile, two CTAs per SM), or
+   * RSLB_PACKED_PERSISTENT (one CTA per SM walking the tiles with two tile
+   * buffers and warp-specialised cell and sweep groups; RSLB_ERR_ARG where it
+   * does not fit: it needs V <= ~700, Z >= RSLB_PACKED_TILE_CELLS + 8).  Both
+   * forms give bitwise identical results. */
   int packed_form;
 } rslb_config;
 

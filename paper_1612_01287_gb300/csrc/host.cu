@@ -366,9 +366,10 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
     return set_error(RSLB_ERR_UNSUPPORTED, "rslb_init: V = %d velocities do not fit one tile", V);
   if (c.packed_form < RSLB_PACKED_AUTO || c.packed_form > RSLB_PACKED_PERSISTENT)
     return set_error(RSLB_ERR_ARG, "rslb_init: unknown packed_form %d", c.packed_form);
-  if (L.B == kSod32Cells && c.packed_form != RSLB_PACKED_PER_TILE) {
-    // the persistent pipelined form where it fits (the population buffers are
-    // cudaMalloc'd, so 16-byte aligned for its bulk-tensor copies)
+  if (L.B == kSod32Cells && c.packed_form == RSLB_PACKED_PERSISTENT) {
+    // the persistent pipelined form on request (the population buffers are
+    // cudaMalloc'd, so 16-byte aligned for its bulk-tensor copies); measured
+    // slower than two CTAs per SM of the per-tile form, so not the default
     SodGeom gq;
     std::memset(&gq, 0, sizeof(gq));
     gq.Z = c.Z;
@@ -379,14 +380,12 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
     int nsm = 0;
     ce = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (ce != cudaSuccess) return cuda_error(ce, "rslb_init: SM count");
-    if (sod32p_fits(gq, max_smem)) {
-      L.form = 1;
-      L.nsm = nsm;
-    } else if (c.packed_form == RSLB_PACKED_PERSISTENT) {
+    if (!sod32p_fits(gq, max_smem))
       return set_error(RSLB_ERR_ARG,
                        "rslb_init: the persistent packed kernel does not fit (V = %d, Z = %d)", V,
                        c.Z);
-    }
+    L.form = 1;
+    L.nsm = nsm;
   } else if (c.packed_form == RSLB_PACKED_PERSISTENT) {
     return set_error(RSLB_ERR_ARG, "rslb_init: packed_form needs the packed FP32 kernel");
   }

@@ -328,14 +328,14 @@ def test_persistent_packed_kernel_is_bitwise_the_per_tile_kernel(Z, Q_xi, bc, ta
     np.testing.assert_array_equal(out["persistent"][1], out["per_tile"][1])
 
 
-def test_persistent_packed_kernel_is_the_default_where_it_fits():
+def test_packed_kernel_forms_are_selected_as_asked():
     from paper_1612_01287_gb300 import RslbError, Sod
     case = dict(Q_xi=200, Q_L=3, N_Omega=5, bc="outflow", tau=1e-2, dt=1e-4)
     with Sod(Z=64, precision="f32", **case) as s:
-        assert s.launch_info() == (PACKED, 512)
-    with Sod(Z=30, precision="f32", **case) as s:  # too short for its bulk copies
         assert s.launch_info() == (PACKED, 8 * PACKED)
-    with pytest.raises(RslbError):
+    with Sod(Z=64, precision="f32", packed_form="persistent", **case) as s:
+        assert s.launch_info() == (PACKED, 512)
+    with pytest.raises(RslbError):  # too short for its bulk copies
         Sod(Z=30, precision="f32", packed_form="persistent", **case)
 
 
