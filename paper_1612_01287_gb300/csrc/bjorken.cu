@@ -522,13 +522,16 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
   b->nblocks = (int)blocks.size();
   b->smem = max_smem;
   // tensor-core work units: runs of equal Q in blocks of at most kTcMaxCols
-  // columns (two CTAs per SM), split evenly, times the M-tiles of K^P
+  // columns (two CTAs per SM), split evenly, times the M-tiles of the even
+  // and odd half-size matrices; the column blocks that share an M-tile are
+  // adjacent, so they stream its image tiles at about the same time
   std::vector<BjTcBlock> tcb;
   std::vector<long long> img_off(qvals.size(), 0);
   long long img_total = 0;
   for (size_t i = 0; i < qvals.size(); ++i) {
     img_off[i] = img_total;
-    img_total += (long long)qvals[i] * ((qvals[i] + 31) / 32) * 64;  // hi and lo tiles
+    const int h = qvals[i] / 2, qh = qvals[i] - h;
+    img_total += bj_tc_image_floats(qh) + bj_tc_image_floats(h);  // E and O, hi and lo
   }
   if (o->kp_mode == RSLB_KP_TF32X3) {
     const int rmax = std::max(1, kTcMaxCols / QL);
@@ -540,26 +543,33 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
       size_t qi = 0;
       while (qvals[qi] != Q) ++qi;
       const int nb = (n + rmax - 1) / rmax;
+      std::vector<BjTcBlock> cols;
       for (int k = 0, done = 0; k < nb; ++k) {
         const int R = (n - done + (nb - k) - 1) / (nb - k);
         BjTcBlock t{};
         t.Q = Q;
+        t.h = Q / 2;
+        t.qh = Q - t.h;
         t.first = s + done;
         t.R = R;
-        t.nmt = (Q + 127) / 128;
+        t.nmt = (t.qh + 127) / 128;
         t.nc = (R * QL + 15) / 16 * 16;
-        t.tmem_cols = 32;
-        while (t.tmem_cols < t.nc) t.tmem_cols *= 2;
+        int half = 32;
+        while (half < t.nc) half *= 2;
+        t.tmem_cols = 2 * half;  // E and O accumulators
         t.soff = roff[s + done];
         t.img = img_off[qi];
+        t.imgO = img_off[qi] + bj_tc_image_floats(t.qh);
         t.xoff = qtab[qi].xi_off;
-        for (int m = 0; m < t.nmt; ++m) {
-          t.mt = m;
-          tcb.push_back(t);
-        }
+        cols.push_back(t);
         tc_smem = std::max(tc_smem, bj_tc_smem_bytes(t.nc, R));
         done += R;
       }
+      for (int m = 0; m < cols[0].nmt; ++m)
+        for (BjTcBlock t : cols) {
+          t.mt = m;
+          tcb.push_back(t);
+        }
       s += n;
     }
     b->ntc = (int)tcb.size();

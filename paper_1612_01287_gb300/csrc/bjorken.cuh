@@ -60,19 +60,38 @@ __device__ inline double kp_entry(int Q, const double* __restrict__ xw,
   return w * (s1 - s2);
 }
 
+// K^P is centrosymmetric, K^P_{Q-1-j, Q-1-j'} = K^P_{j j'} (the nodes are
+// symmetric and P_m(-x) = (-1)^m P_m(x); every term pairs P_m with P_m or
+// P_{m+-2}).  With h = floor(Q/2) mirror pairs and qh = ceil(Q/2), the even
+// and odd parts of a column f,
+//   s_j = f_j + f_{Q-1-j} (j < h),  s_h = f_h for odd Q  (j < qh),
+//   d_j = f_j - f_{Q-1-j}                                (j < h),
+// give K^P f through two half-size products:
+//   (K f)_j + (K f)_{Q-1-j} = sum_j' E_{j j'} s_j',  E_{j j'} = K_{j j'} + K_{j, Q-1-j'},
+//   (K f)_j - (K f)_{Q-1-j} = sum_j' O_{j j'} d_j',  O_{j j'} = K_{j j'} - K_{j, Q-1-j'},
+// for j < h (E also for the middle row j = h of odd Q, where it gives twice
+// (K f)_h).  E is qh x qh, O is h x h: half the flops and half the image.
+//
 // Work unit of the tensor-core stage kernel: the runs [first, first + R)
 // (sorted order, all with Q_xi = Q, states contiguous from soff) and the
-// M-tile mt (rows j = 128 mt .. 128 mt + 127 of K^P).
+// M-tile mt (rows i = 128 mt .. 128 mt + 127 of E and O).
 struct BjTcBlock {
   int Q, first, R, mt;
-  int nmt;         // M-tiles of Q: ceil(Q / 128)
+  int nmt;         // M-tiles: ceil(qh / 128)
   int nc;          // MMA N: R * Q_L rounded up to a multiple of 16
-  int tmem_cols;   // TMEM columns allocated (power of two >= max(nc, 32))
+  int tmem_cols;   // TMEM columns allocated: two accumulators (E, O) of a
+                   // power of two >= max(nc, 32) columns each
+  int qh, h;       // rows of E (ceil(Q/2)) and of O (floor(Q/2))
   int pad;
   long long soff;  // state offset (floats) of run `first`
-  long long img;   // offset (floats) of the K^P image of this Q
+  long long img;   // offset (floats) of the E image of this Q
+  long long imgO;  // offset (floats) of the O image of this Q
   long long xoff;  // offset of [xi | w] of this Q in the node pool
 };
+
+// Floats of the split, swizzled image of an n x n matrix (n rows of
+// ceil(n/32) tiles of 32 columns, hi and lo parts).
+__host__ __device__ inline long long bj_tc_image_floats(int n) { return (long long)n * ((n + 31) / 32) * 64; }
 
 struct BjTcArgs {
   const BjTcBlock* blocks;

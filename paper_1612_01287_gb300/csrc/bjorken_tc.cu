@@ -140,14 +140,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_wait_ld() {
@@ -178,9 +174,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   extern __shared__ unsigned char smem_raw[];
   const BjTcBlock blk = a.blocks[blockIdx.x];
   const int Q = blk.Q, R = blk.R, NC = blk.nc, mt = blk.mt;
+  const int qh = blk.qh, hp = blk.h;  // rows of E and of O
   const int ncv = R * QL;
-  const int nkb = (Q + 31) / 32;
-  const int rows = min(128, Q - 128 * mt);
+  const int nkbE = (qh + 31) / 32;
+  const int rowsE = min(128, qh - 128 * mt);
+  const int rowsO = max(0, min(128, hp - 128 * mt));
+  const int nkbOf = (hp + 31) / 32;         // K-blocks of the O image
+  const int nkbO = rowsO > 0 ? nkbOf : 0;   // K-blocks of O this M-tile computes
+  const int nkb = nkbE + nkbO;              // even K-blocks first, then odd
+  const uint32_t dodd = (uint32_t)blk.tmem_cols / 2;  // column of the O accumulator
   const uint32_t btile = (uint32_t)NC * 128u;
   const uint32_t sstride = 2 * kATile + 2 * btile;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -199,14 +201,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   float* rs = reinterpret_cast<float*>(tail + 64);  // rate[R] | neq4[R] | omt[R]
   float* mp = rs + 3 * R;                           // [4 warps][R][2]
 
-  // zero the rows of the A buffers that the copies do not fill (past the
-  // end of K^P in a partial M-tile), set up barriers
+  // zero the rows of the A buffers that the copies of the shorter image (O,
+  // rowsO <= rowsE) do not fill; rows past rowsE stay zero, rows in
+  // [rowsO, rowsE) only reach rows of the O accumulator that are not read
   {
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int s = 0; s < 2; ++s)
-      for (int h = 0; h < 2; ++h) {
-        float4* z = reinterpret_cast<float4*>(base + s * sstride + h * kATile);
-        for (int i = rows * 8 + tid; i < (int)(kATile / 16); i += kTcThreads) z[i] = zero;
+      for (int hh = 0; hh < 2; ++hh) {
+        float4* z = reinterpret_cast<float4*>(base + s * sstride + hh * kATile);
+        for (int i = rowsO * 8 + tid; i < (int)(kATile / 16); i += kTcThreads) z[i] = zero;
       }
   }
   if (tid == 0) {
@@ -231,11 +234,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // tile (mt, kb): hi at Asrc + kb * rows * 64, lo rows * 32 floats after it
-  const float* Asrc = a.kimg + blk.img + (size_t)mt * 128 * nkb * 64;
-  const uint32_t abytes = (uint32_t)rows * 128u;
+  // E tile (mt, kb): hi at AsrcE + kb * rowsE * 64, lo rowsE * 32 floats after
+  // it; O tiles likewise from AsrcO
+  const float* AsrcE = a.kimg + blk.img + (size_t)mt * 128 * nkbE * 64;
+  const float* AsrcO = a.kimg + blk.imgO + (size_t)mt * 128 * nkbOf * 64;
   auto copy_a = [&](int s, int it) {
-    const float* src = Asrc + (size_t)it * rows * 64;
+    const bool ev = it < nkbE;
+    const int rows = ev ? rowsE : rowsO;
+    const float* src = ev ? AsrcE + (size_t)it * rows * 64 : AsrcO + (size_t)(it - nkbE) * rows * 64;
+    const uint32_t abytes = (uint32_t)rows * 128u;
     mbar_expect_tx(&full[s], 2 * abytes);
     bulk_g2s(Ahi(s), src, abytes, &full[s]);
     bulk_g2s(Alo(s), src + (size_t)rows * 32, abytes, &full[s]);
@@ -293,16 +300,23 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   }
 
   // what the epilogue needs from global memory, loaded before the K-loop so
-  // the latency is not paid after it: row j of D per worker thread
-  const int j = 128 * mt + 32 * (warp & 3) + lane;
-  const bool rowok = j < Q;
-  float xi2 = 0.f, wj = 0.f;
+  // the latency is not paid after it.  Worker thread i (row i of E and O)
+  // writes rows j1 = i and, if i < h, j2 = Q - 1 - i of K^P f.
+  const int i = 128 * mt + 32 * (warp & 3) + lane;
+  const bool okE = i < qh, okO = i < hp;
+  const int j1 = i, j2 = Q - 1 - i;
+  float xi2a = 0.f, wja = 0.f, xi2b = 0.f, wjb = 0.f;
   float KL[QL * QL], xk[QL], wk[QL], l1[QL];
   if (warp < 4) {
-    if (rowok) {
-      const double x = a.npool[blk.xoff + j];
-      xi2 = float(x * x);
-      wj = float(a.npool[blk.xoff + Q + j]);
+    if (okE) {
+      const double x = a.npool[blk.xoff + j1];
+      xi2a = float(x * x);
+      wja = float(a.npool[blk.xoff + Q + j1]);
+    }
+    if (okO) {
+      const double x = a.npool[blk.xoff + j2];
+      xi2b = float(x * x);
+      wjb = float(a.npool[blk.xoff + Q + j2]);
     }
 #pragma unroll
     for (int k = 0; k < QL; ++k) {
@@ -314,12 +328,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
     }
   }
 
-  // ---- main loop over K-blocks of 32 rows j' ----
-  // Workers (warps 0-3): store the state rows of K-block it (loaded into
-  // registers during it-1) split into hi/lo, load those of it+1 and arrive
-  // on ready[s].  Issuer: wait full[s] (the K^P tiles) and ready[s], issue
-  // the 12 MMAs, commit to done[s]; once they are done, refill stage s with
-  // the K^P tiles of it+2.  No CTA-wide barrier inside the loop.
+  // ---- main loop over K-blocks of 32 rows j' (E, then O) ----
+  // Workers (warps 0-3): store the even (s) or odd (d) parts of the state
+  // rows of K-block it (loaded into registers during it-1) split into hi/lo,
+  // load those of it+1 and arrive on ready[s].  Issuer: wait full[s] (the
+  // image tiles) and ready[s], issue the 12 MMAs into the E or O
+  // accumulator, commit to done[s]; once they are done, refill stage s with
+  // the tiles of it+2.  No CTA-wide barrier inside the loop.
   const float* Fblk = a.Fin + blk.soff;
   int lost = 0;
   if (issuer) {
@@ -331,13 +346,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
         break;
       }
       tc_fence_after();
+      const bool ev = it < nkbE;
+      const uint32_t dacc = ev ? tmem : tmem + dodd;
+      const int k0 = ev ? it : it - nkbE;
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
         const uint64_t ah = sdesc(su32(Ahi(s)) + 32u * ks), al = sdesc(su32(Alo(s)) + 32u * ks);
         const uint64_t bh = sdesc(su32(Bhi(s)) + 32u * ks), bl = sdesc(su32(Blo(s)) + 32u * ks);
-        mma_tf32(tmem, ah, bh, idesc, (it > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32(tmem, ah, bl, idesc, 1u);
-        mma_tf32(tmem, al, bh, idesc, 1u);
+        mma_tf32(dacc, ah, bh, idesc, (k0 > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(dacc, ah, bl, idesc, 1u);
+        mma_tf32(dacc, al, bh, idesc, 1u);
       }
       mma_commit(&done[s]);
       last_commit = it;
@@ -353,11 +371,21 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   } else if (warp < 4) {
     float bv[kTcMaxRowsPerWarp];
     auto load_b = [&](int it) {
-      const int jj = it * 32 + lane;
+      const bool ev = it < nkbE;
+      const int jj = (ev ? it : it - nkbE) * 32 + lane;
 #pragma unroll
       for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
         const int c = warp + 4 * u;
-        bv[u] = (c < ncv && jj < Q) ? Fblk[(size_t)c * Q + jj] : 0.f;
+        float v = 0.f;
+        if (c < ncv) {
+          const float* col = Fblk + (size_t)c * Q;
+          if (ev) {
+            if (jj < qh) v = jj < hp ? col[jj] + col[Q - 1 - jj] : col[jj];
+          } else if (jj < hp) {
+            v = col[jj] - col[Q - 1 - jj];
+          }
+        }
+        bv[u] = v;
       }
     };
     load_b(0);
@@ -409,7 +437,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   }
   tc_fence_after();
 
-  // ---- epilogue (worker warps): row j of D per thread ----
+  // ---- epilogue (worker warps): rows j1 = i and j2 = Q-1-i per thread ----
+  // (K f)_{j1} = (Y_E + Y_O)/2, (K f)_{j2} = (Y_E - Y_O)/2 (Y_O = 0 past h)
   if (warp < 4) {
     const float itau = float(1.0 / a.tau), dt = float(a.dtau);
     const float ca = a.stage == 1 ? 0.75f : 1.f / 3.f, cb = a.stage == 1 ? 0.25f : 2.f / 3.f;
@@ -417,59 +446,73 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
     const float* Fin = a.Fin + blk.soff;
     const float* Fn = a.Fn + blk.soff;
     float* Fout = a.Fout + blk.soff;
-    for (int rb = 0; rb < R; rb += 16) {
+    constexpr int RG = 4;  // runs per TMEM read
+    for (int rb = 0; rb < R; rb += RG) {
       const int c0 = rb * QL;
-      uint32_t d[16 * QL];
+      uint32_t de[RG * QL], dd[RG * QL];
 #pragma unroll
       for (int p = 0; p < QL; ++p)
-        if (c0 + 16 * p < NC) tmem_ld16(trow + (uint32_t)(c0 + 16 * p), d + 16 * p);
+        if (c0 + RG * p < NC) {
+          tmem_ld4(trow + (uint32_t)(c0 + RG * p), de + RG * p);
+          tmem_ld4(trow + dodd + (uint32_t)(c0 + RG * p), dd + RG * p);
+        }
       tmem_wait_ld();
-      // four runs at a time: all their loads of f^(i) and f_n are issued
-      // before any of their stores (the output may alias f_n, so the loads of
-      // a later run could not move above the stores of an earlier one)
+      // four runs at a time: all their loads of f^(i) and f_n (both rows) are
+      // issued before any of their stores (the output may alias f_n)
 #pragma unroll
-      for (int g = 0; g < 16; g += 4) {
-        float fk[4][QL], fnv[4][QL];
+      for (int g = 0; g < RG; g += 4) {
+        float fk[2][4][QL], fnv[2][4][QL];
 #pragma unroll
-        for (int ii = 0; ii < 4; ++ii) {
-          const int r = rb + g + ii;
+        for (int w2 = 0; w2 < 2; ++w2) {
+          const bool ok = w2 == 0 ? okE : okO;
+          const int jr = w2 == 0 ? j1 : j2;
 #pragma unroll
-          for (int k = 0; k < QL; ++k) {
-            const size_t o = (size_t)(r * QL + k) * Q + j;
-            const bool ok = r < R && rowok;
-            fk[ii][k] = ok ? Fin[o] : 0.f;
-            fnv[ii][k] = (ok && rk && a.stage != 0) ? Fn[o] : 0.f;
+          for (int ii = 0; ii < 4; ++ii) {
+            const int r = rb + g + ii;
+#pragma unroll
+            for (int k = 0; k < QL; ++k) {
+              const size_t o = (size_t)(r * QL + k) * Q + jr;
+              const bool okr = r < R && ok;
+              fk[w2][ii][k] = okr ? Fin[o] : 0.f;
+              fnv[w2][ii][k] = (okr && rk && a.stage != 0) ? Fn[o] : 0.f;
+            }
           }
         }
         float mv[8];  // (N, E) partials of the four runs
 #pragma unroll
         for (int ii = 0; ii < 4; ++ii) {
-          const int i = g + ii, r = rb + i;
+          const int cidx = g + ii, r = rb + cidx;
           float on = 0.f, oe = 0.f;
-          if (r < R && rowok) {
-            if (!rk) {
 #pragma unroll
-              for (int k = 0; k < QL; ++k)
-                a.dout[blk.soff + (size_t)(r * QL + k) * Q + j] = __uint_as_float(d[i * QL + k]);
-            } else {
-              const float rate = rs[r], neq4 = rs[R + r], omt = rs[2 * R + r];
+          for (int w2 = 0; w2 < 2; ++w2) {
+            const bool ok = w2 == 0 ? okE : okO;
+            const int jr = w2 == 0 ? j1 : j2;
+            const float xi2 = w2 == 0 ? xi2a : xi2b, wj = w2 == 0 ? wja : wjb;
+            if (r < R && ok) {
 #pragma unroll
               for (int k = 0; k < QL; ++k) {
-                float klf = 0.f;
+                const float ye = __uint_as_float(de[cidx * QL + k]);
+                const float yo = okO ? __uint_as_float(dd[cidx * QL + k]) : 0.f;
+                const float kpf = 0.5f * (w2 == 0 ? ye + yo : ye - yo);
+                const size_t o = (size_t)(r * QL + k) * Q + jr;
+                if (!rk) {
+                  a.dout[blk.soff + o] = kpf;
+                } else {
+                  const float rate = rs[r], neq4 = rs[R + r], omt = rs[2 * R + r];
+                  float klf = 0.f;
 #pragma unroll
-                for (int q = 0; q < QL; ++q) klf += KL[k * QL + q] * fk[ii][q];
-                const float feq = neq4 * (wj * wk[k]) * (1.f + l1[k] * omt);
-                const float L =
-                    (-fk[ii][k] + xi2 * klf + __uint_as_float(d[i * QL + k])) * itau -
-                    (fk[ii][k] - feq) * rate;
-                const float v = fk[ii][k] + dt * L;
-                const size_t o = (size_t)(r * QL + k) * Q + j;
-                float out = v;
-                if (a.stage == 1) out = ca * fnv[ii][k] + cb * v;
-                else if (a.stage == 2) out = fnv[ii][k] * ca + cb * v;
-                Fout[o] = out;
-                on += out;
-                oe += xk[k] * out;
+                  for (int q = 0; q < QL; ++q) klf += KL[k * QL + q] * fk[w2][ii][q];
+                  const float feq = neq4 * (wj * wk[k]) * (1.f + l1[k] * omt);
+                  const float L = (-fk[w2][ii][k] + xi2 * klf + kpf) * itau -
+                                  (fk[w2][ii][k] - feq) * rate;
+                  const float v = fk[w2][ii][k] + dt * L;
+                  float out = v;
+                  if (a.stage == 1) out = ca * fnv[w2][ii][k] + cb * v;
+                  else if (a.stage == 2) out = fnv[w2][ii][k] * ca + cb * v;
+                  Fout[o] = out;
+                  on += out;
+                  oe += xk[k] * out;
+                }
               }
             }
           }
@@ -481,16 +524,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
           // with the level's bit set keep the upper half of their values and
           // trade the lower half with the partner lane (9 shuffles, not 40)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int q = 0; q < 4; ++q) {
             const bool up = lane & 16;
-            const float send = up ? mv[i] : mv[i + 4], keep = up ? mv[i + 4] : mv[i];
-            mv[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            const float send = up ? mv[q] : mv[q + 4], keep = up ? mv[q + 4] : mv[q];
+            mv[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
           }
 #pragma unroll
-          for (int i = 0; i < 2; ++i) {
+          for (int q = 0; q < 2; ++q) {
             const bool up = lane & 8;
-            const float send = up ? mv[i] : mv[i + 2], keep = up ? mv[i + 2] : mv[i];
-            mv[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            const float send = up ? mv[q] : mv[q + 2], keep = up ? mv[q + 2] : mv[q];
+            mv[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
           }
           {
             const bool up = lane & 4;
@@ -528,22 +571,29 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   }
 }
 
-// K^P image of one Q, split for 3xTF32: tile (mt, kb) = rows j in M-tile mt
-// (rows(mt) of them) x columns j' = 32 kb .. 32 kb + 31; its hi part
-// tf32(K) (round to nearest) is stored swizzled at
-// img + (mt * 128 * nkb + kb * rows(mt)) * 64 floats and its lo part K - hi
-// (exact in FP32) rows(mt) * 32 floats after it.  Columns j' >= Q stay zero
-// (the buffer is cleared first).
+// Images of one Q, split for 3xTF32: the even matrix E (qh x qh) at img and
+// the odd matrix O (h x h) after it (see BjTcBlock).  Tile (mt, kb) of an
+// n x n matrix = rows i in M-tile mt (rows(mt) of them) x columns
+// 32 kb .. 32 kb + 31; its hi part tf32(X) (round to nearest) is stored
+// swizzled at (mt * 128 * nkb + kb * rows(mt)) * 64 floats and its lo part
+// X - hi (exact in FP32) rows(mt) * 32 floats after it.  Columns past n stay
+// zero (the buffer is cleared first).  Entries from FP64 K^P (Eq. K_leg_disc).
 __global__ void bj_tc_image_kernel(int Q, const double* __restrict__ xw,
                                    const double* __restrict__ kc, float* img) {
-  const int nkb = (Q + 31) / 32;
+  const int h = Q / 2, qh = Q - h;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Q * Q) return;
-  const int j = idx / Q, jp = idx - j * Q;
-  const int mt = j >> 7, row = j & 127, kb = jp >> 5, col = jp & 31;
-  const int rows = min(128, Q - 128 * mt);
-  float* tile = img + ((size_t)mt * 128 * nkb + (size_t)kb * rows) * 64;
-  const float x = float(kp_entry(Q, xw, kc, j, jp));
+  if (idx >= qh * qh + h * h) return;
+  const bool odd = idx >= qh * qh;
+  const int n = odd ? h : qh;
+  const int e = odd ? idx - qh * qh : idx;
+  const int i = e / n, jp = e - i * n;
+  const double k1 = kp_entry(Q, xw, kc, i, jp), k2 = kp_entry(Q, xw, kc, i, Q - 1 - jp);
+  const float x = float(odd ? k1 - k2 : k1 + k2);
+  const int nkb = (n + 31) / 32;
+  const int mt = i >> 7, row = i & 127, kb = jp >> 5, col = jp & 31;
+  const int rows = min(128, n - 128 * mt);
+  float* tile = img + (odd ? bj_tc_image_floats(qh) : 0) + ((size_t)mt * 128 * nkb +
+                                                            (size_t)kb * rows) * 64;
   const float hi = tf32_rn(x);
   tile[swz(row, col) >> 2] = hi;
   tile[(size_t)rows * 32 + (swz(row, col) >> 2)] = x - hi;
@@ -601,7 +651,7 @@ cudaError_t bj_tc_stage_launch(const BjTcArgs& a, int nblocks, size_t smem, cuda
 
 cudaError_t bj_tc_image_launch(int Q, const double* xw, const double* kc, float* img,
                                cudaStream_t st) {
-  const int n = Q * Q;
+  const int n = (Q - Q / 2) * (Q - Q / 2) + (Q / 2) * (Q / 2);
   bj_tc_image_kernel<<<(n + 255) / 256, 256, 0, st>>>(Q, xw, kc, img);
   return cudaGetLastError();
 }

@@ -154,3 +154,34 @@ def test_kp_from_the_coefficient_table(Q):
     K = oracle.kp_matrix(Q)
     got = np.array([[_kp_entry_from_table(Q, xi, w, j, jp) for jp in range(Q)] for j in range(Q)])
     assert np.abs(got - K).max() <= 1e-12 * np.abs(K).max()
+
+
+@pytest.mark.parametrize("Q", [8, 9, 20, 33, 64, 129, 200])
+def test_kp_even_odd_split_reproduces_kp(Q):
+    """The tensor-core contraction uses K^P's centrosymmetry (K_{Q-1-j, Q-1-j'} =
+    K_{j j'}, Eq. K_leg_disc on symmetric nodes): with h = floor(Q/2) mirror pairs
+    and qh = ceil(Q/2), E_{ij} = K_{ij} + K_{i,Q-1-j} (qh x qh) acting on the even
+    parts s_j = f_j + f_{Q-1-j} (s_h = f_h for odd Q) and O_{ij} = K_{ij} - K_{i,Q-1-j}
+    (h x h) acting on the odd parts d_j = f_j - f_{Q-1-j} give
+    (K f)_i = (E s + O d)_i / 2 and (K f)_{Q-1-i} = (E s - O d)_i / 2 (i < h), and
+    (K f)_h = (E s)_h / 2 for the middle row.  Restated here in numpy on the
+    oracle's K^P."""
+    K = oracle.kp_matrix(Q)
+    J = K[::-1, ::-1]
+    assert np.array_equal(K, J), "K^P is exactly centrosymmetric in FP64"
+    h, qh = Q // 2, Q - Q // 2
+    E = K[:qh, :qh] + K[:qh, ::-1][:, :qh]
+    O = K[:h, :h] - K[:h, ::-1][:, :h]
+    rng = np.random.default_rng(Q)
+    f = rng.normal(size=(Q, 3))
+    s = f[:qh].copy()
+    s[:h] += f[::-1][:h]
+    d = f[:h] - f[::-1][:h]
+    ye, yo = E @ s, O @ d
+    y = np.empty_like(f)
+    y[:h] = 0.5 * (ye[:h] + yo)
+    y[Q - 1 - np.arange(h)] = 0.5 * (ye[:h] - yo)
+    if Q % 2:
+        y[h] = 0.5 * ye[h]
+    ref = K @ f
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(K).sum(1).max() * np.abs(f).max()
