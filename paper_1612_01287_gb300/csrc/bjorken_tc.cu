@@ -181,7 +181,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   const int rowsO = max(0, min(128, hp - 128 * mt));
   const int nkbOf = (hp + 31) / 32;         // K-blocks of the O image
   const int nkbO = rowsO > 0 ? nkbOf : 0;   // K-blocks of O this M-tile computes
-  const int nkb = nkbE + nkbO;              // even K-blocks first, then odd
+  const int nkb = nkbE + nkbO;
+  // iteration order: even and odd K-blocks of the same 32 rows j' alternate
+  // (E kb, O kb, E kb+1, ...) while both exist, then the remaining even ones,
+  // so the workers load each pair f_j', f_{Q-1-j'} once for both parts
+  auto kb_of = [&](int it) { return it < 2 * nkbO ? it >> 1 : it - nkbO; };
+  auto odd_of = [&](int it) { return it < 2 * nkbO && (it & 1); };
   const uint32_t dodd = (uint32_t)blk.tmem_cols / 2;  // column of the O accumulator
   const uint32_t btile = (uint32_t)NC * 128u;
   const uint32_t sstride = 2 * kATile + 2 * btile;
@@ -239,9 +244,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   const float* AsrcE = a.kimg + blk.img + (size_t)mt * 128 * nkbE * 64;
   const float* AsrcO = a.kimg + blk.imgO + (size_t)mt * 128 * nkbOf * 64;
   auto copy_a = [&](int s, int it) {
-    const bool ev = it < nkbE;
+    const bool ev = !odd_of(it);
     const int rows = ev ? rowsE : rowsO;
-    const float* src = ev ? AsrcE + (size_t)it * rows * 64 : AsrcO + (size_t)(it - nkbE) * rows * 64;
+    const float* src = (ev ? AsrcE : AsrcO) + (size_t)kb_of(it) * rows * 64;
     const uint32_t abytes = (uint32_t)rows * 128u;
     mbar_expect_tx(&full[s], 2 * abytes);
     bulk_g2s(Ahi(s), src, abytes, &full[s]);
@@ -257,6 +262,20 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
     for (int it = 0; it < 2 && it < nkb; ++it) {
       copy_a(it, it);
       last_copy = it;
+    }
+    // the block's state (its runs are contiguous) is read by the K-loop
+    // (both halves of every column) and by the epilogue: bring f^(i) and f_n
+    // into L2 at once (the 16-byte-aligned interior of each region)
+    const size_t nst = (size_t)ncv * Q;
+    const float* regs[2] = {a.Fin + blk.soff, a.Fn + blk.soff};
+    for (int q = 0; q < (a.stage > 0 ? 2 : 1); ++q) {
+      const uintptr_t b0 = reinterpret_cast<uintptr_t>(regs[q]);
+      const uintptr_t e0 = reinterpret_cast<uintptr_t>(regs[q] + nst);
+      const uintptr_t b1 = (b0 + 15) & ~uintptr_t(15), e1 = e0 & ~uintptr_t(15);
+      if (e1 > b1)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b1),
+                     "r"((uint32_t)(e1 - b1))
+                     : "memory");
     }
   }
 
@@ -328,10 +347,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
     }
   }
 
-  // ---- main loop over K-blocks of 32 rows j' (E, then O) ----
+  // ---- main loop over K-blocks of 32 rows j' (E and O alternating) ----
   // Workers (warps 0-3): store the even (s) or odd (d) parts of the state
-  // rows of K-block it (loaded into registers during it-1) split into hi/lo,
-  // load those of it+1 and arrive on ready[s].  Issuer: wait full[s] (the
+  // rows of K-block it (the pair loaded into registers earlier) split into
+  // hi/lo, load the next pair after its last use and arrive on ready[s].  Issuer: wait full[s] (the
   // image tiles) and ready[s], issue the 12 MMAs into the E or O
   // accumulator, commit to done[s]; once they are done, refill stage s with
   // the tiles of it+2.  No CTA-wide barrier inside the loop.
@@ -346,9 +365,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
         break;
       }
       tc_fence_after();
-      const bool ev = it < nkbE;
-      const uint32_t dacc = ev ? tmem : tmem + dodd;
-      const int k0 = ev ? it : it - nkbE;
+      const uint32_t dacc = odd_of(it) ? tmem + dodd : tmem;
+      const int k0 = kb_of(it);
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
         const uint64_t ah = sdesc(su32(Ahi(s)) + 32u * ks), al = sdesc(su32(Alo(s)) + 32u * ks);
@@ -369,26 +387,32 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
       }
     }
   } else if (warp < 4) {
-    float bv[kTcMaxRowsPerWarp];
-    auto load_b = [&](int it) {
-      const bool ev = it < nkbE;
-      const int jj = (ev ? it : it - nkbE) * 32 + lane;
+    // fa, fb: f_j' and f_{Q-1-j'} of the current K-block pair; after the even
+    // part s is stored, fa holds the odd part d until its iteration
+    float fa[kTcMaxRowsPerWarp], fb[kTcMaxRowsPerWarp];
+    auto load_pair = [&](int kb) {
+      const int jj = kb * 32 + lane;
 #pragma unroll
       for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
         const int c = warp + 4 * u;
-        float v = 0.f;
-        if (c < ncv) {
-          const float* col = Fblk + (size_t)c * Q;
-          if (ev) {
-            if (jj < qh) v = jj < hp ? col[jj] + col[Q - 1 - jj] : col[jj];
-          } else if (jj < hp) {
-            v = col[jj] - col[Q - 1 - jj];
-          }
-        }
-        bv[u] = v;
+        const float* col = Fblk + (size_t)c * Q;
+        fa[u] = (c < ncv && jj < qh) ? col[jj] : 0.f;
+        fb[u] = (c < ncv && jj < hp) ? col[Q - 1 - jj] : 0.f;
       }
     };
-    load_b(0);
+    auto store_b = [&](int s, const float* v) {
+#pragma unroll
+      for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
+        const int c = warp + 4 * u;
+        if (c < NC) {
+          const float hi = tf32_rn(v[u]);
+          const uint32_t o = swz(c, lane);
+          *reinterpret_cast<float*>(Bhi(s) + o) = hi;
+          *reinterpret_cast<float*>(Blo(s) + o) = v[u] - hi;
+        }
+      }
+    };
+    load_pair(0);
     for (int it = 0; it < nkb; ++it) {
       const int s = it & 1;
       // stage s was last read by the MMAs of it-2
@@ -396,17 +420,23 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
         lost = 1;
         break;
       }
+      const int kb = kb_of(it);
+      const bool has_odd = kb < nkbO;
+      if (!odd_of(it)) {
+        // even part s_j' = f_j' + f_{Q-1-j'} (the middle row of odd Q alone)
+        const int jj = kb * 32 + lane;
 #pragma unroll
-      for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
-        const int c = warp + 4 * u;
-        if (c < NC) {
-          const float hi = tf32_rn(bv[u]);
-          const uint32_t o = swz(c, lane);
-          *reinterpret_cast<float*>(Bhi(s) + o) = hi;
-          *reinterpret_cast<float*>(Blo(s) + o) = bv[u] - hi;
+        for (int u = 0; u < kTcMaxRowsPerWarp; ++u) {
+          const float f1 = fa[u], f2 = fb[u];
+          fb[u] = jj < hp ? f1 + f2 : f1;
+          fa[u] = f1 - f2;  // odd part d_j' (zero past h: f2 = 0 there, unused)
         }
+        store_b(s, fb);
+        if (!has_odd && it + 1 < nkb) load_pair(kb_of(it + 1));
+      } else {
+        store_b(s, fa);
+        if (it + 1 < nkb) load_pair(kb_of(it + 1));
       }
-      if (it + 1 < nkb) load_b(it + 1);
       fence_proxy_async();
       mbar_arrive(&ready[s]);
     }
