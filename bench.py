@@ -205,9 +205,13 @@ def measured_peak():
 KERNEL_SOURCES = {
     # the sources a stage kernel is compiled from
     "sod32_stage_kernel": ("paper_1612_01287_gb300/csrc/sod32.cu",
+                           "paper_1612_01287_gb300/csrc/sod32_core.cuh",
                            "paper_1612_01287_gb300/csrc/sod.cuh",
                            "paper_1612_01287_gb300/csrc/rslb_device.cuh", "include/rslb.h"),
 }
+KERNEL_SOURCES["sod_stage_kernel<double,16>"] = (
+    "paper_1612_01287_gb300/csrc/sod.cu", "paper_1612_01287_gb300/csrc/sod.cuh",
+    "paper_1612_01287_gb300/csrc/rslb_device.cuh")
 # of these headers the kernel uses only the lines that match
 KERNEL_SOURCE_LINES = {"include/rslb.h": re.compile(r"^#define RSLB_PACKED_TILE_CELLS\b")}
 
@@ -266,6 +270,19 @@ def recorded_traffic(kernel):
     return None
 
 
+def recorded_fp64_ops(kernel):
+    """FP64-pipe lane operations per cell-velocity and stage of an FP64 stage
+    kernel, from the last ncu count, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path)).get(kernel)
+        if d and d.get("source_sha") == source_sha(kernel):
+            return d.get("fp64_lane_ops_per_cv_stage")
+    except Exception:
+        pass
+    return None
+
+
 HBARC_GEV_FM = 0.1973269804
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
@@ -301,8 +318,16 @@ def bench_bjorken(stream, steps=None):
     qxi, eta_s, T0 = workloads.bjorken_batch(nruns=ARGS.bj_runs)
     taus = 5 * HBARC_GEV_FM * eta_s / (0.5 * T0)
     cv = 3 * int(qxi.sum())
-    flops = 3 * 2 * 3 * float((qxi.astype(np.float64) ** 2).sum())  # K^P contraction only
-    out = {"runs": len(qxi), "cv_per_step": cv, "kp_flops_per_step": flops}
+    q = qxi.astype(np.float64)
+    # the method's contraction K^P f as a dense product: 2 Q^2 flops per radial
+    # column, 3 columns per run, 3 RK stages per step
+    flops = 3 * 2 * 3 * float((q ** 2).sum())
+    # what the tensor cores execute: the even (ceil(Q/2)^2) and odd (floor(Q/2)^2)
+    # half-size products, three TF32 products each (hi.hi, hi.lo, lo.hi)
+    qh, h = np.ceil(q / 2), np.floor(q / 2)
+    pipe_flops = 3 * 3 * 2 * 3 * float((qh ** 2 + h ** 2).sum())
+    out = {"runs": len(qxi), "cv_per_step": cv, "kp_flops_per_step": flops,
+           "tensor_pipe_flops_per_step": pipe_flops}
     for mode in ARGS.bj_modes.split(","):
         with Bjorken(qxi, "parton", taus, Q_L=3, precision="f32", kp_mode=mode, dtau=1e-3,
                      stream=stream) as b:
@@ -318,11 +343,16 @@ def bench_bjorken(stream, steps=None):
             # the contraction as a tensor-core roofline: three TF32 products per
             # FP32 product (hi.hi, hi.lo, lo.hi) against the dense TF32 peak
             peak = measured_tf32_peak()
-            pipe = 3 * flops / (ms * 1e-3) / 1e12
+            pipe = pipe_flops / (ms * 1e-3) / 1e12
+            useful = flops / (ms * 1e-3) / 1e12
             out[mode]["tensor_roofline"] = {
                 "bound": "tensor", "achieved": pipe, "unit": "TFLOP/s",
                 "peak": peak, "frac": pipe / peak if peak else None,
-                "peak_source": "measured bf16 x 1/2" if peak else None}
+                "peak_source": "measured bf16 x 1/2" if peak else None,
+                "useful_tflops": useful, "useful_frac": useful / peak if peak else None,
+                "note": "achieved counts the TF32 products the tensor pipe executes (three per "
+                        "FP32 product, half-size even/odd matrices); useful counts the dense "
+                        "FP32 product K^P f once"}
     return out
 
 
@@ -663,8 +693,20 @@ def run_ours(args, rank, world, local_rank):
             b.record(stream)
             torch.cuda.synchronize()
             fms = a.elapsed_time(b) / 2
+            from paper_1612_01287_gb300._lib import measure_fp64_fma
+            dfma = measure_fp64_fma(20, stream)
             fp64 = {"value": V * Z / (fms * 1e-3), "unit": UNIT, "ms_per_tube_step": fms,
-                    "note": "one tube, FP64 everywhere; bound by the FP64 pipe, not HBM"}
+                    "note": "one tube, FP64 everywhere; bound by the FP64 pipe, not HBM",
+                    "measured_dfma_per_s": dfma}
+            ops = recorded_fp64_ops("sod_stage_kernel<double,16>")
+            if ops:
+                # FP64 lane operations the kernel executes (ncu, per cell-velocity and
+                # stage) against the measured DFMA lane rate: the FP64-pipe roofline
+                ach = ops * V * Z * 3 / (fms * 1e-3)
+                fp64["roofline"] = {"bound": "fp64", "achieved": ach / 1e9, "peak": dfma / 1e9,
+                                    "unit": "G FP64 lane-ops/s", "frac": ach / dfma,
+                                    "ops_per_cv_stage": ops,
+                                    "kernel": "sod_stage_kernel<double,16>"}
 
     B_tile = tubes[0].launch_info()[0]
     from paper_1612_01287_gb300._lib import PACKED_TILE_CELLS

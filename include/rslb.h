@@ -49,6 +49,8 @@ extern "C" {
 #define RSLB_ERR_NONPHYSICAL 6  /* a cell left the physical domain (n, E <= 0,
                                    |beta| >= 1, non-finite) */
 #define RSLB_ERR_UNSUPPORTED 7  /* size beyond what the kernels support */
+#define RSLB_ERR_TIMEOUT 8      /* a bounded wait inside a kernel ran out (the
+                                   kernel left its work and freed what it held) */
 
 /* ---- enumerations ---- */
 #define RSLB_F32 0 /* populations, fluxes, relaxation in FP32; Landau in FP64 */
@@ -391,6 +393,18 @@ int rslb_bjorken_set_state(rslb_bjorken* b, const void* f);
  */
 int rslb_bjorken_kp_apply(rslb_bjorken* b, void* y);
 
+/*
+ * Self-test of the tensor-core kernel's failure handling (not part of the
+ * method): one contraction-only launch in which the worker warps never signal
+ * that their operand tiles are ready, so the issuing thread's bounded wait
+ * (~0.3 s) runs out.  Each CTA then records the time-out, waits (bounded) for
+ * the copies it issued, frees its tensor memory and returns; the state is
+ * untouched and the handle stays usable.  Expected result: RSLB_ERR_TIMEOUT.
+ * Synchronises.  Errors: RSLB_ERR_ARG, RSLB_ERR_UNSUPPORTED (kp_mode other than
+ * RSLB_KP_TF32X3), RSLB_ERR_CUDA, RSLB_ERR_TIMEOUT.
+ */
+int rslb_bjorken_selftest_timeout(rslb_bjorken* b);
+
 /* Release everything owned by b (synchronises).  NULL is a no-op. */
 void rslb_bjorken_destroy(rslb_bjorken* b);
 
@@ -485,6 +499,19 @@ int rslb_closure_sample(rslb_handle* hi, rslb_handle* lo, double tau, float* X, 
  * (3V+1) -> V.  Asynchronous.
  */
 int rslb_closure_step(rslb_handle* lo, rslb_mlp* m, double tau, int nsteps);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement support (not part of the method).                            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * FP64 fused multiply-add rate of the current device: reps launches of
+ * 8 x (SM count) blocks of 256 threads, each thread running 8 independent
+ * DFMA chains of 4096 steps, timed with CUDA events on `stream` (after one
+ * untimed launch).  *fma_per_s receives DFMA operations (lanes) per second.
+ * Changes no device setting.  Errors: RSLB_ERR_ARG, RSLB_ERR_CUDA.
+ */
+int rslb_measure_fp64_fma(int reps, double* fma_per_s, void* stream);
 
 /* Description of the last failure in the calling thread ("" if none). */
 const char* rslb_last_error(void);

@@ -232,6 +232,18 @@ def sod_step_noalloc(f_ptr, nsteps, Z, Q_xi, Q_L=3, N_Omega=None, z_min=-1.0, z_
     _check(fn(ctypes.byref(cfg), ctypes.c_void_p(f_ptr), int(nsteps), _stream_ptr(stream)))
 
 
+def measure_fp64_fma(reps=20, stream=None):
+    """DFMA lane operations per second of the current device
+    (``rslb_measure_fp64_fma``)."""
+    L = load()
+    fn = L.rslb_measure_fp64_fma
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    out = ctypes.c_double()
+    _check(fn(int(reps), ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
+
+
 BJ_FIELDS = ("tau", "n", "E", "P", "T", "Pi", "PL", "PT")
 GAS = {"parton": 0, "ideal": 1}
 KP = {"simt": 0, "tf32x3": 2}
@@ -317,6 +329,15 @@ class Bjorken:
     def set_state(self, f):
         f = np.ascontiguousarray(f, dtype=self.dtype)
         _check(load().rslb_bjorken_set_state(self._h, _ptr(f)))
+
+    def selftest_timeout(self):
+        """Run the tensor-core kernel's failure-handling self-test
+        (``rslb_bjorken_selftest_timeout``); returns its status code
+        (RSLB_ERR_TIMEOUT = 8 expected) and message without raising."""
+        L = load()
+        rc = L.rslb_bjorken_selftest_timeout(self._h)
+        msg = L.rslb_last_error()
+        return rc, msg.decode() if msg else ""
 
     def kp_apply(self):
         """K^P f of every run's current state (tensor-core path), like get_state."""

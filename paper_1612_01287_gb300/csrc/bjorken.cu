@@ -391,6 +391,10 @@ int bj_check_err(rslb_bjorken* b) {
     cudaMemsetAsync(b->err, 0, 2 * sizeof(int), b->stream);
     cudaStreamSynchronize(b->stream);
     const int user = (herr[1] >= 0 && herr[1] < b->nruns) ? b->user_of_sorted[herr[1]] : -1;
+    if (herr[0] == RSLB_ERR_TIMEOUT)
+      return set_error(RSLB_ERR_TIMEOUT,
+                       "rslb_bjorken: a bounded wait in the tensor-core kernel ran out (run %d)",
+                       user);
     return set_error(RSLB_ERR_NONPHYSICAL, "rslb_bjorken: non-physical state in run %d", user);
   }
   return RSLB_OK;
@@ -802,6 +806,38 @@ extern "C" int rslb_bjorken_set_state(rslb_bjorken* b, const void* f) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_error(e, "rslb_bjorken_set_state");
   return RSLB_OK;
+}
+
+extern "C" int rslb_bjorken_selftest_timeout(rslb_bjorken* b) {
+  clear_error();
+  if (!b) return set_error(RSLB_ERR_ARG, "rslb_bjorken_selftest_timeout: NULL argument");
+  if (b->kp_mode != RSLB_KP_TF32X3)
+    return set_error(RSLB_ERR_UNSUPPORTED, "rslb_bjorken_selftest_timeout: needs RSLB_KP_TF32X3");
+  // one contraction-only launch (it writes nothing but the scratch buffer)
+  // in which the worker warps never arrive on the operand-ready barriers
+  BjTcArgs a{};
+  a.blocks = b->tcblocks;
+  a.kimg = b->kimg;
+  a.npool = b->npool;
+  a.tau_aw0 = b->tau_aw0;
+  a.gas = b->gas;
+  a.xk = b->xk;
+  a.wk = b->wk;
+  a.KL = b->KL;
+  a.QL = b->QL;
+  a.stage = -1;
+  a.Fin = (const float*)b->state;
+  a.Fn = (const float*)b->state;
+  a.mp_in = b->mp[b->mp_cur];
+  a.dout = b->ytmp;
+  a.tau = 1.0;
+  a.dtau = b->dtau;
+  a.err = b->err;
+  a.withhold_ready = 1;
+  cudaError_t e = bj_tc_stage_launch(a, b->ntc, b->tc_smem, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_error(e, "rslb_bjorken_selftest_timeout");
+  return bj_check_err(b);
 }
 
 extern "C" int rslb_bjorken_kp_apply(rslb_bjorken* b, void* y) {

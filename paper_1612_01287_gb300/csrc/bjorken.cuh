@@ -112,6 +112,8 @@ struct BjTcArgs {
   float* dout;            // stage -1 only
   double tau, dtau;       // stage time and step
   int* err;
+  int withhold_ready;     // failure-handling self-test: the workers never
+                          // signal that their operand tiles are ready
 };
 
 // Largest MMA N (state columns per block) of the tensor-core stage kernel.

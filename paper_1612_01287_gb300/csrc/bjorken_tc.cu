@@ -40,7 +40,7 @@ constexpr int kTcWorkers = 128;
 constexpr uint32_t kATile = 128 * 128;  // bytes: 128 rows x 32 FP32
 constexpr int kSpinLimit = 150000;       // try_wait rounds of at most kSuspendNs: ~0.3 s
 constexpr uint32_t kSuspendNs = 2000;
-constexpr int kErrTimeout = 97;
+constexpr int kErrTimeout = RSLB_ERR_TIMEOUT;
 constexpr int kTcMaxRowsPerWarp = kTcMaxCols / 4;  // state rows per warp in a K-block
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
         if (it + 1 < nkb) load_pair(kb_of(it + 1));
       }
       fence_proxy_async();
-      mbar_arrive(&ready[s]);
+      if (!a.withhold_ready) mbar_arrive(&ready[s]);
     }
     // the last commit completes after all earlier MMAs
     if (!lost && !mbar_wait(&done[(nkb - 1) & 1], (uint32_t)((nkb - 1) >> 1) & 1u)) lost = 1;

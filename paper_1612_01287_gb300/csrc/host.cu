@@ -279,6 +279,9 @@ int check_device_error(rslb_handle* h) {
   if (herr[0] != 0) {
     cudaMemsetAsync(h->d_err, 0, 2 * sizeof(int), h->stream);
     cudaStreamSynchronize(h->stream);
+    if (herr[0] == RSLB_ERR_TIMEOUT)
+      return set_error(RSLB_ERR_TIMEOUT, "a bounded wait in a stage kernel ran out (tile at cell %d)",
+                       herr[1]);
     return set_error(RSLB_ERR_NONPHYSICAL,
                      "non-physical state (n, E <= 0, |beta| >= 1 or non-finite) in cell %d",
                      herr[1]);

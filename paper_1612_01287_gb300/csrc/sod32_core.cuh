@@ -39,7 +39,7 @@ constexpr int kCellThreads = 8 * kB2;  // moments: a warp per 4 cells; coefficie
 static_assert(kB2 % 4 == 0 && kH % 2 == 0 && (kC / 4) % 2 == 1, "packed tile shape");
 constexpr int kMP = 8;        // coefficient pitch (m) for N_Omega <= 7
 constexpr int kInflight = 8;  // 16-byte global loads in flight per thread (staging, store)
-constexpr int kErrWait = 97;  // error code: a bounded wait ran out
+constexpr int kErrWait = RSLB_ERR_TIMEOUT;  // error code: a bounded wait ran out
 
 __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }

@@ -98,3 +98,28 @@ def test_tf32x3_tracks_simt_fp32():
         a, c = res[0][k], res[1][k]
         assert np.abs(a - c).max() <= 1e-5 * np.abs(a).max(), k
     assert np.abs(res[1]["n"] * res[1]["tau"] - 1).max() < 1e-5
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable():
+    """Failure handling of the tensor-core kernel: in a self-test launch the
+    worker warps never signal their operand tiles (a flag that nothing sets).
+    The issuing thread's bounded mbarrier wait runs out; every CTA records the
+    time-out, waits for the copies it issued, frees its tensor memory and
+    returns.  The host reads RSLB_ERR_TIMEOUT; the same handle then steps and
+    matches the oracle as if nothing had happened."""
+    import time
+    from paper_1612_01287_gb300 import Bjorken
+    Qs, taus = [8, 33, 130], [0.05, 0.5, math.inf]
+    with Bjorken(Qs, "parton", taus, Q_L=3, precision="f32", kp_mode="tf32x3", dtau=1e-2) as b:
+        t0 = time.perf_counter()
+        rc, msg = b.selftest_timeout()
+        waited = time.perf_counter() - t0
+        assert rc == 8, (rc, msg)
+        assert "bounded wait" in msg
+        assert waited < 30.0
+        b.step(20)
+        got = b.read()
+    ref, _ = oracle_batch(Qs, ["parton"] * 3, taus, 20)
+    e = errors(got, ref)
+    for k, v in e.items():
+        assert v <= 1e-5, (k, e)
