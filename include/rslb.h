@@ -251,9 +251,16 @@ void rslb_destroy(rslb_handle* h);
 typedef struct rslb_sod_run {
   int Z;                  /* cells */
   int Q_xi;               /* polar nodes */
-  double tau;             /* constant relaxation time > 0 */
+  double tau;             /* RSLB_TAU_CONST: constant relaxation time > 0 */
   double nL, TL, nR, TR;  /* chambers at rest (Sec. IV A) */
   double t_end;           /* final time > 0 */
+  int tau_mode;           /* RSLB_TAU_CONST, RSLB_TAU_ETAS or RSLB_TAU_NONE */
+  double tau_AW0;         /* RSLB_TAU_ETAS: tau_AW0 > 0 (Eq. Sod:tau) */
+  double lambda_ref;      /* RSLB_TAU_ETAS: lambda_ref > 0 */
+  int N_Omega;            /* f^eq truncation of this run; -1: the batch's rule */
+  double dt;              /* > 0: this time step (t_end is rounded to whole steps;
+                             required unless tau_mode is RSLB_TAU_CONST);
+                             0: automatic (see rslb_sod_batch_init) */
 } rslb_sod_run;
 
 typedef struct rslb_sod_batch_opts {
@@ -270,9 +277,10 @@ typedef struct rslb_sod_batch_opts {
 typedef struct rslb_sod_batch rslb_sod_batch;
 
 /*
- * Set up nruns shock tubes.  Each run gets dt = t_end / ceil(t_end / dt_max)
- * with dt_max = min(cfl dz / max|xi|, dt_over_tau * tau), i.e. it reaches
- * t_end exactly after its own number of steps.  Runs are grouped by velocity
+ * Set up nruns shock tubes.  A run with dt = 0 (constant tau only) gets
+ * dt = t_end / ceil(t_end / dt_max) with dt_max = min(cfl dz / max|xi|,
+ * dt_over_tau * tau), i.e. it reaches t_end exactly after its own number of
+ * steps; a run with dt > 0 takes round(t_end / dt) steps of dt.  Runs are grouped by velocity
  * count; each group is advanced by one persistent launch per RK stage that
  * walks the tiles of its runs (runs with fewer steps drop out as they
  * finish).  With autotune, the tile kernel and CTAs per SM of each group are

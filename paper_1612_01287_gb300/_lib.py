@@ -367,7 +367,9 @@ class SodRun(ctypes.Structure):
     """Mirror of ``rslb_sod_run``."""
     _fields_ = [("Z", ctypes.c_int), ("Q_xi", ctypes.c_int), ("tau", ctypes.c_double),
                 ("nL", ctypes.c_double), ("TL", ctypes.c_double), ("nR", ctypes.c_double),
-                ("TR", ctypes.c_double), ("t_end", ctypes.c_double)]
+                ("TR", ctypes.c_double), ("t_end", ctypes.c_double), ("tau_mode", ctypes.c_int),
+                ("tau_AW0", ctypes.c_double), ("lambda_ref", ctypes.c_double),
+                ("N_Omega", ctypes.c_int), ("dt", ctypes.c_double)]
 
 
 class SodBatchOpts(ctypes.Structure):
@@ -401,8 +403,10 @@ def _batch_sigs(L):
 class SodBatch:
     """Many independent shock tubes advanced together (``rslb_sod_batch``).
 
-    ``runs``: sequence of dicts with keys Z, Q_xi, tau, t_end and optionally
-    nL, TL, nR, TR (default: the chambers of Sec. IV A)."""
+    ``runs``: sequence of dicts with keys Z, Q_xi, t_end and tau (constant
+    relaxation time) or tau_mode "etas" with tau_AW0, lambda_ref and dt, and
+    optionally nL, TL, nR, TR (default: the chambers of Sec. IV A), N_Omega,
+    dt."""
 
     def __init__(self, runs, Q_L=3, N_Omega=-1, precision="f32", bc="outflow", z_min=-1.0,
                  z_max=1.0, cfl=0.5, dt_over_tau=0.5, autotune=True, stream=None):
@@ -411,9 +415,13 @@ class SodBatch:
         n = len(runs)
         arr = (SodRun * n)()
         for r, R in enumerate(runs):
-            arr[r] = SodRun(int(R["Z"]), int(R["Q_xi"]), float(R["tau"]), float(R.get("nL", 1.0)),
-                            float(R.get("TL", 1.0)), float(R.get("nR", 0.125)),
-                            float(R.get("TR", 0.8)), float(R["t_end"]))
+            tm = R.get("tau_mode", "const")
+            arr[r] = SodRun(int(R["Z"]), int(R["Q_xi"]), float(R.get("tau", 0.0)),
+                            float(R.get("nL", 1.0)), float(R.get("TL", 1.0)),
+                            float(R.get("nR", 0.125)), float(R.get("TR", 0.8)),
+                            float(R["t_end"]), TAU[tm] if isinstance(tm, str) else int(tm),
+                            float(R.get("tau_AW0", 0.0)), float(R.get("lambda_ref", 1.0)),
+                            int(R.get("N_Omega", -1)), float(R.get("dt", 0.0)))
         if precision not in ("f32", "fp32", "f64", "fp64", F32, F64):
             raise ValueError("precision must be 'f32' or 'f64'")
         self.fp64 = precision in ("f64", "fp64", F64)

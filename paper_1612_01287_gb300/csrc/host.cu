@@ -985,28 +985,43 @@ extern "C" int rslb_sod_batch_init(rslb_sod_batch** out, const rslb_sod_run* run
   int rc = RSLB_OK;
   for (int r = 0; r < nruns && !rc; ++r) {
     const rslb_sod_run& R = runs[r];
-    if (R.Z < 1 || R.Q_xi < 2 || !(R.tau > 0.0) || !(R.t_end > 0.0)) {
+    const bool tconst = R.tau_mode == RSLB_TAU_CONST;
+    if (R.Z < 1 || R.Q_xi < 2 || !(R.t_end > 0.0) || R.tau_mode < RSLB_TAU_CONST ||
+        R.tau_mode > RSLB_TAU_NONE || (tconst && !(R.tau > 0.0)) ||
+        (R.tau_mode == RSLB_TAU_ETAS && !(R.tau_AW0 > 0.0 && R.lambda_ref > 0.0)) ||
+        !(R.dt >= 0.0) || (!tconst && !(R.dt > 0.0)) || R.N_Omega < -1) {
       rc = set_error(RSLB_ERR_ARG, "rslb_sod_batch_init: run %d: invalid parameters", r);
       break;
     }
-    std::vector<double> xi(R.Q_xi), w(R.Q_xi);
-    gauss_legendre_host(R.Q_xi, xi.data(), w.data());
-    const double dz = (o->z_max - o->z_min) / R.Z;
-    const double dtmax = std::fmin(o->cfl * dz / std::fabs(xi[R.Q_xi - 1]), o->dt_over_tau * R.tau);
-    const long long ns = (long long)std::ceil(R.t_end / dtmax - 1e-12);
+    long long ns;
+    double dt;
+    if (R.dt > 0.0) {
+      ns = std::max(1LL, (long long)std::llround(R.t_end / R.dt));
+      dt = R.dt;
+    } else {
+      std::vector<double> xi(R.Q_xi), w(R.Q_xi);
+      gauss_legendre_host(R.Q_xi, xi.data(), w.data());
+      const double dz = (o->z_max - o->z_min) / R.Z;
+      const double dtmax =
+          std::fmin(o->cfl * dz / std::fabs(xi[R.Q_xi - 1]), o->dt_over_tau * R.tau);
+      ns = (long long)std::ceil(R.t_end / dtmax - 1e-12);
+      dt = R.t_end / (double)ns;
+    }
     rslb_config c{};
     c.Z = R.Z;
     c.z_min = o->z_min;
     c.z_max = o->z_max;
     c.Q_xi = R.Q_xi;
     c.Q_L = o->Q_L;
-    c.N_Omega = o->N_Omega >= 0 ? o->N_Omega : std::min(R.Q_xi - 1, 5);
+    c.N_Omega = R.N_Omega >= 0 ? R.N_Omega
+                               : (o->N_Omega >= 0 ? o->N_Omega : std::min(R.Q_xi - 1, 5));
     c.precision = o->precision;
     c.bc = o->bc;
-    c.tau_mode = RSLB_TAU_CONST;
+    c.tau_mode = R.tau_mode;
     c.tau = R.tau;
-    c.lambda_ref = 1.0;
-    c.dt = R.t_end / (double)ns;
+    c.tau_AW0 = R.tau_AW0;
+    c.lambda_ref = R.tau_mode == RSLB_TAU_ETAS ? R.lambda_ref : 1.0;
+    c.dt = dt;
     c.nL = R.nL;
     c.TL = R.TL;
     c.nR = R.nR;
