@@ -192,3 +192,33 @@ HBARC_GEV_FM = 0.1973269804  # hbar c in GeV fm
 def tau_aw0_bjorken(eta_s, T0_GeV, tau0_fm):
     """tau_AW0 = 5 hbar (eta/s) / (tau0 k_B T0) in units of tau0 (Eq. bjorken_tauAW)."""
     return 5.0 * HBARC_GEV_FM * eta_s / (tau0_fm * T0_GeV)
+
+
+# ---------------------------------------------------------------------------
+# Sec. IV B 2: integrated heat flux and shear stress near the inviscid limit
+# ---------------------------------------------------------------------------
+def dissipation_integrals(nL, TL, nR, TR, tau_coef_etas, lambda_ref=1.0, method="ce"):
+    """Eqs. intq and intpi: the integrals of q over the contact and the shock
+    and of Pi over the shock, from the inviscid plateau states (Eqs. Sod:PC -
+    Sod:nII), T = P/n, the relative fugacity lambda_bar = P/T^4 = n/T^3,
+    tau_AW = tau_AW0/T [1 - ln(lambda_bar lambda_ref)/4] (Eq. Sod:tau) and the
+    Chapman-Enskog (eta = 4/5 P tau_AW, lambda_heat = 4/3 P tau_AW/T, Eq.
+    tcoeff_ce) or Grad (2/3 and 4/5, Eq. tcoeff_grad) transport coefficients."""
+    R = Riemann(nL, nL * TL, nR, nR * TR)
+    PC, vC, vS = R.PC, R.beta_C, R.beta_shock
+    gC2 = 1.0 / (1.0 - vC * vC)
+    ce, cl = (4.0 / 5.0, 4.0 / 3.0) if method == "ce" else (2.0 / 3.0, 4.0 / 5.0)
+
+    def state(n, P):
+        T = P / n
+        lam = n / T**3
+        tau = tau_coef_etas / T * (1.0 - 0.25 * math.log(lam * lambda_ref))
+        return T, lam, ce * P * tau, cl * P * tau / T
+
+    T1, l1, e1, k1 = state(R.nI, PC)
+    T2, l2, e2, k2 = state(R.nII, PC)
+    TR_, lR, eR, kR = state(nR, nR * TR)
+    q_c = (k1 * T1 + k2 * T2) * math.log(l2 / l1) / 8.0
+    q_s = (kR * TR_ + k2 * T2 * gC2 * (1.0 - vC * vS)) * math.log(lR / l2) / 8.0
+    pi_s = 2.0 * vC * math.sqrt(gC2) / 3.0 * (eR + e2 * (1.0 - vC * vS))
+    return {"q_contact": q_c, "q_shock": q_s, "Pi_shock": pi_s, "zeta_C": vC, "zeta_S": vS}

@@ -1,0 +1,109 @@
+"""Integrated heat flux and shear stress across the contact discontinuity and
+the shock (Sec. IV B 2, Eqs. intq and intpi): the closed forms pinned by
+integrating the hydrodynamic expressions (Eqs. q_inv, pi_inv) over smoothed
+discontinuities, and the GPU tubes near the inviscid limit against the
+Chapman-Enskog values."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import exact
+
+STATE = dict(nL=1.0, TL=1.0, nR=0.125, TR=0.5)  # Eq. Sod:right_adim
+
+
+def test_closed_forms_from_smoothed_inviscid_profiles():
+    """Eqs. q_inv and pi_inv written as g(zeta) dh/dzeta (t q: g = kappa T gamma^2
+    (1 - beta zeta)/4, h = ln lambda_bar; t Pi: g = -(4 eta/3)(1 - beta zeta),
+    h = gamma beta) with the transport coefficients of each inviscid state, g and
+    h smoothed across the contact and the shock by one common sigmoid and
+    integrated numerically: Eqs. intq and intpi (via Eq. int_disc)."""
+    tc = 0.0385  # tau_AW0 = 0.3854 eta/s at eta/s = 0.1 (scale only)
+    ref = exact.dissipation_integrals(**STATE, tau_coef_etas=tc)
+    R = exact.Riemann(1.0, 1.0, 0.125, 0.0625)
+    zC, zS = ref["zeta_C"], ref["zeta_S"]
+    w = 2e-4
+    x = np.linspace(-1.0, 1.0, 2_000_001)
+    dz = x[1] - x[0]
+
+    def props(n, P, beta, z0):
+        T = P / n
+        lam = n / T**3
+        tau = tc / T * (1.0 - 0.25 * math.log(lam))
+        g2 = 1.0 / (1.0 - beta * beta)
+        eta, kap = 0.8 * P * tau, 4.0 / 3.0 * P * tau / T
+        return {"gq": kap * T * g2 * (1.0 - beta * z0) / 4.0, "hq": math.log(lam),
+                "gp": -4.0 * eta / 3.0 * (1.0 - beta * z0), "hp": math.sqrt(g2) * beta}
+
+    for z0, name, (l, r) in ((zC, "contact", ((R.nI, R.PC, R.beta_C), (R.nII, R.PC, R.beta_C))),
+                             (zS, "shock", ((R.nII, R.PC, R.beta_C), (0.125, 0.0625, 0.0)))):
+        a, b = props(*l, z0), props(*r, z0)
+        S = 0.5 * (1.0 + np.tanh((x - z0) / w))
+        f = {k: a[k] + (b[k] - a[k]) * S for k in a}
+        m = np.abs(x - z0) < 40 * w
+        iq = np.trapezoid((f["gq"] * np.gradient(f["hq"], dz))[m], x[m])
+        ipi = np.trapezoid((f["gp"] * np.gradient(f["hp"], dz))[m], x[m])
+        if name == "contact":
+            assert iq == pytest.approx(ref["q_contact"], rel=1e-6)
+            assert abs(ipi) < 1e-14
+        else:
+            assert iq == pytest.approx(ref["q_shock"], rel=1e-6)
+            assert ipi == pytest.approx(ref["Pi_shock"], rel=1e-6)
+
+
+def test_windows_integral_midpoint():
+    from paper_1612_01287_gb300.dissipation import window_integral
+    z = (np.arange(100) + 0.5) / 100
+    assert window_integral(z, np.ones(100), 0.2, 0.4) == pytest.approx(0.2)
+    assert window_integral(z, z, 0.0, 1.0) == pytest.approx(0.5)
+
+
+def windows(t):
+    zC, zS = exact.dissipation_integrals(**STATE, tau_coef_etas=1.0)["zeta_C"], \
+        exact.dissipation_integrals(**STATE, tau_coef_etas=1.0)["zeta_S"]
+    return {"contact": (zC * t - 0.05, zC * t + 0.05), "shock": (zS * t - 0.05, zS * t + 0.05)}
+
+
+@pytest.mark.gpu
+def test_gpu_tubes_match_oracle_integrals():
+    """The batched FP64 engine and the oracle give the same window integrals on
+    a coarse grid (Z = 400, t = 0.25)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_01287_gb300.dissipation import sod_dissipation_integrals, window_integral
+    etas, t = [1e-2], 0.25
+    res = sod_dissipation_integrals(etas, windows(t), Z=400, dt=1.25e-4, t_end=t)
+    p = oracle.sod_params(400, 6, 2, 5, z_min=-0.5, z_max=0.5, bc="fixed_eq", tau_mode="etas",
+                          tau_AW0=0.3854e-2, lambda_ref=1.0, dt=1.25e-4,
+                          left=(1.0, 1.0, 0.0), right=(0.125, 0.5, 0.0))
+    m = oracle.sod_moments(p, oracle.sod_steps(p, oracle.sod_init_riemann(p), 2000))
+    for name, (lo, hi) in windows(t).items():
+        for k in ("q", "Pi"):
+            want = window_integral(res["z"], m[k], lo, hi)
+            assert res[name][k][0] == pytest.approx(want, rel=1e-9, abs=1e-13), (name, k)
+
+
+@pytest.mark.gpu
+def test_near_inviscid_integrals_follow_chapman_enskog():
+    """Q_xi = 6, Q_L = 2, N_Omega = 5 tubes at eta/s = 5e-3 and 1e-2 (Z = 4000,
+    t = 0.5): the integrated q (contact, shock) and Pi (shock) lie close to the
+    Chapman-Enskog predictions (Eqs. intq, intpi) and closer to them than to
+    Grad's (the paper's finding, Sec. IV B 2)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_01287_gb300.dissipation import sod_dissipation_integrals
+    etas, t = [5e-3, 1e-2], 0.5
+    res = sod_dissipation_integrals(etas, windows(t), Z=4000, dt=1.25e-5, t_end=t)
+    for i, es in enumerate(etas):
+        ce = exact.dissipation_integrals(**STATE, tau_coef_etas=0.3854 * es)
+        gr = exact.dissipation_integrals(**STATE, tau_coef_etas=0.3854 * es, method="grad")
+        got = {"q_contact": res["contact"]["q"][i], "q_shock": res["shock"]["q"][i],
+               "Pi_shock": res["shock"]["Pi"][i]}
+        print("eta/s", es, {k: (got[k], ce[k], gr[k]) for k in got})
+        for k in got:
+            assert abs(got[k] / ce[k] - 1.0) < 0.25, (es, k, got[k], ce[k])
+            assert abs(got[k] - ce[k]) < abs(got[k] - gr[k]), (es, k, got[k], ce[k], gr[k])
