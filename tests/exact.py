@@ -222,3 +222,78 @@ def dissipation_integrals(nL, TL, nR, TR, tau_coef_etas, lambda_ref=1.0, method=
     q_s = (kR * TR_ + k2 * T2 * gC2 * (1.0 - vC * vS)) * math.log(lR / l2) / 8.0
     pi_s = 2.0 * vC * math.sqrt(gC2) / 3.0 * (eR + e2 * (1.0 - vC * vS))
     return {"q_contact": q_c, "q_shock": q_s, "Pi_shock": pi_s, "zeta_C": vC, "zeta_S": vS}
+
+
+# ---------------------------------------------------------------------------
+# Sec. V C: semi-analytic solution of the relaxation-time Bjorken flow of a
+# parton gas (Eqs. flork_sol, flork_sol_aux)
+# ---------------------------------------------------------------------------
+def _H(y):
+    """H(y) = y^2 + arctan(sqrt(y^-2 - 1))/sqrt(y^-2 - 1) for 0 < y <= 1."""
+    y = np.asarray(y, dtype=float)
+    s = np.sqrt(np.maximum(1.0 / (y * y) - 1.0, 0.0))
+    ss = np.where(s > 1e-4, s, 1.0)
+    at = np.where(s > 1e-4, np.arctan(ss) / ss, 1.0 - s * s / 3.0 + s**4 / 5.0)
+    return y * y + at
+
+
+def _HL(y):
+    """H_L(y) = y^2 d/dy [H(y)/y] = y H'(y) - H(y), with H' from its closed form:
+    d/dy [arctan(s)/s] = (ds/dy)(1/(s (1 + s^2)) - arctan(s)/s^2), s = sqrt(y^-2 - 1),
+    ds/dy = -1/(y^3 s)."""
+    y = np.asarray(y, dtype=float)
+    s = np.sqrt(np.maximum(1.0 / (y * y) - 1.0, 0.0))
+    big = s > 1e-3
+    ss = np.where(big, s, 1.0)
+    dterm = np.where(big, (-1.0 / (y**3 * ss)) * (1.0 / (ss * (1.0 + ss * ss)) - np.arctan(ss) / ss**2),
+                     # series of arctan(s)/s = 1 - s^2/3 + s^4/5 with s^2 = y^-2 - 1
+                     (2.0 / (3.0 * y**3)) - (4.0 / 5.0) * (1.0 / y**2 - 1.0) / y**3)
+    Hp = 2.0 * y + dterm
+    return y * Hp - _H(y)
+
+
+def florkowski_parton(tau_AW0, tau_f=40.0, dtau=0.04, tol=1e-7, max_iter=500):
+    """(tau, T, n, P_L) of Eqs. flork_sol by the iteration the paper describes:
+    T_(0) = tau^(-1/3), trapezoidal quadrature on an equidistant grid, stop
+    when the L2 norm (over [1, tau_f]) of T_(n) - T_(n-1) is below tol.
+    Parton gas: tau_AW = tau_AW0 / T, P = T^4."""
+    tau = np.arange(1.0, tau_f + 0.5 * dtau, dtau)
+    N = len(tau)
+    T = tau ** (-1.0 / 3.0)
+
+    def cumtrap(f):
+        out = np.zeros(N)
+        out[1:] = np.cumsum(0.5 * (f[1:] + f[:-1]) * dtau)
+        return out
+
+    H1 = _H(1.0)
+    for _ in range(max_iter):
+        I = cumtrap(T)  # int_1^tau T
+        T4 = np.empty(N)
+        src = T**4 * T / (2.0 * tau_AW0)  # T^4 / (2 tau_AW), tau_AW = tau_AW0 / T
+        for i in range(N):
+            D = np.exp(-(I[i] - I[: i + 1]) / tau_AW0)  # D(tau_i, tau')
+            g = src[: i + 1] * D * _H(tau[: i + 1] / tau[i])
+            integral = 0.5 * dtau * (g[1:] + g[:-1]).sum() if i > 0 else 0.0
+            T4[i] = D[0] * _H(1.0 / tau[i]) / H1 + integral
+        Tn = T4**0.25
+        L2 = math.sqrt(_trap((Tn - T) ** 2, dtau) / (tau_f - 1.0))
+        T = Tn
+        if L2 <= tol:
+            break
+    I = cumtrap(T)
+    n = np.empty(N)
+    PL = np.empty(N)
+    for i in range(N):
+        D = np.exp(-(I[i] - I[: i + 1]) / tau_AW0)
+        gn = T[: i + 1] ** 3 * tau[: i + 1] * T[: i + 1] / tau_AW0 * D
+        gp = T[: i + 1] ** 5 / (2.0 * tau_AW0) * D * _HL(tau[: i + 1] / tau[i])
+        In = 0.5 * dtau * (gn[1:] + gn[:-1]).sum() if i > 0 else 0.0
+        Ip = 0.5 * dtau * (gp[1:] + gp[:-1]).sum() if i > 0 else 0.0
+        n[i] = (D[0] + In) / tau[i]
+        PL[i] = 3.0 * (D[0] * _HL(1.0 / tau[i]) / H1 + Ip)
+    return tau, T, n, PL
+
+
+def _trap(f, h):
+    return float(0.5 * h * (f[1:] + f[:-1]).sum())

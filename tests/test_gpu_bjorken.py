@@ -106,3 +106,33 @@ def test_density_conservation_ideal_gas():
         b.step(100)
         o = b.read()
     assert np.abs(o["n"] * o["tau"] - 1).max() < 1e-12
+
+
+@pytest.mark.parametrize("precision,kp_mode,tol", [("f64", "simt", 1e-4), ("f32", "tf32x3", 1e-4)])
+def test_transition_regime_against_florkowski(precision, kp_mode, tol):
+    """4 pi eta/s = 1, 3, 10 at T0 = 0.3 GeV (Sec. V C): T and P_L/P_T of the GPU
+    runs (Q_xi = 40, Q_L = 3, dtau = 1e-3, tau to 10) against the semi-analytic
+    solution of Eqs. flork_sol."""
+    import math
+    from paper_1612_01287_gb300 import Bjorken
+    from tests import exact
+    e4 = [1.0, 3.0, 10.0]
+    taus = [exact.tau_aw0_bjorken(e / (4 * math.pi), 0.3, 0.5) for e in e4]
+    ref = [exact.florkowski_parton(t, tau_f=10.0, dtau=0.01) for t in taus]
+    marks = [1.0 + 0.5 * k for k in range(1, 19)]
+    got = []
+    with Bjorken([40] * 3, "parton", taus, Q_L=3, precision=precision, kp_mode=kp_mode,
+                 dtau=1e-3) as b:
+        done = 0
+        for m in marks:
+            n = int(round((m - 1.0) / 1e-3)) - done
+            b.step(n)
+            done += n
+            got.append(b.read())
+    for r in range(3):
+        tau, T, _, PL = ref[r]
+        for m, o in zip(marks, got):
+            i = int(round((m - 1.0) / 0.01))
+            PT = (3 * T[i] ** 4 - PL[i]) / 2
+            assert abs(o["T"][r] / T[i] - 1) < tol, (e4[r], m)
+            assert abs(o["PL"][r] / o["PT"][r] - PL[i] / PT) < tol, (e4[r], m)

@@ -598,3 +598,30 @@ def test_bjorken_rk3_third_order():
         _, h = oracle.bjorken_run(p(dt), ns)
         errs.append(abs(h["P"][-1] - href["P"][-1]))
     assert 6.0 < errs[0] / errs[1] < 10.0, errs
+
+
+# ------------------------------------------- Florkowski semi-analytic Bjorken
+def test_florkowski_solution_free_streaming_limit():
+    """Eqs. flork_sol with tau_AW0 -> infinity reduce to the ballistic solution
+    (Eq. bjorken_bal): T^4 = P, P_L as printed, n tau = 1."""
+    tau, T, n, PL = exact.florkowski_parton(1e8, tau_f=5.0, dtau=0.01)
+    P, PLb = exact.bjorken_ballistic(tau)
+    assert np.abs(T**4 - P).max() < 1e-7
+    assert np.abs(PL - PLb).max() < 1e-6
+    assert np.abs(n * tau - 1.0).max() < 1e-6
+
+
+@pytest.mark.parametrize("eta_s_4pi", [1.0, 3.0, 10.0])
+def test_bjorken_parton_matches_florkowski_semianalytic(eta_s_4pi):
+    """Transition regime (Sec. V C, Fig. bjorken_flork): the FP64 oracle with
+    Q_xi = 40, Q_L = 3, dtau = 1e-3 against the iterative solution of Eqs.
+    flork_sol (T0 = 0.3 GeV, tau0 = 0.5 fm/c, tau to 10): T, n and P_L/P_T."""
+    t0 = exact.tau_aw0_bjorken(eta_s_4pi / (4 * math.pi), 0.3, 0.5)
+    tau, T, n, PL = exact.florkowski_parton(t0, tau_f=10.0, dtau=0.01)
+    p = oracle.bjorken_params(40, 3, gas="parton", tau_AW0=t0, dtau=1e-3)
+    _, h = oracle.bjorken_run(p, 9000)
+    idx = np.round((tau - 1.0) / 1e-3).astype(int)
+    PT = (3 * T**4 - PL) / 2
+    assert np.abs(h["T"][idx] / T - 1).max() < 1e-4
+    assert np.abs(h["n"][idx] / n - 1).max() < 2e-4
+    assert np.abs(h["PL"][idx] / h["PT"][idx] - PL / PT).max() < 1e-4
