@@ -209,7 +209,7 @@ KERNEL_SOURCES = {
                            "paper_1612_01287_gb300/csrc/sod.cuh",
                            "paper_1612_01287_gb300/csrc/rslb_device.cuh", "include/rslb.h"),
 }
-KERNEL_SOURCES["sod_stage_kernel<double,16>"] = (
+KERNEL_SOURCES["sod_stage_kernel<double,8>"] = KERNEL_SOURCES["sod_stage_kernel<double,16>"] = (
     "paper_1612_01287_gb300/csrc/sod.cu", "paper_1612_01287_gb300/csrc/sod.cuh",
     "paper_1612_01287_gb300/csrc/rslb_device.cuh")
 # of these headers the kernel uses only the lines that match
@@ -698,15 +698,18 @@ def run_ours(args, rank, world, local_rank):
             fp64 = {"value": V * Z / (fms * 1e-3), "unit": UNIT, "ms_per_tube_step": fms,
                     "note": "one tube, FP64 everywhere; bound by the FP64 pipe, not HBM",
                     "measured_dfma_per_s": dfma}
-            ops = recorded_fp64_ops("sod_stage_kernel<double,16>")
+            k64 = "sod_stage_kernel<double,%d>" % t64.launch_info()[0]
+            ops = recorded_fp64_ops(k64)
             if ops:
                 # FP64 lane operations the kernel executes (ncu, per cell-velocity and
                 # stage) against the measured DFMA lane rate: the FP64-pipe roofline
                 ach = ops * V * Z * 3 / (fms * 1e-3)
                 fp64["roofline"] = {"bound": "fp64", "achieved": ach / 1e9, "peak": dfma / 1e9,
                                     "unit": "G FP64 lane-ops/s", "frac": ach / dfma,
-                                    "ops_per_cv_stage": ops,
-                                    "kernel": "sod_stage_kernel<double,16>"}
+                                    "ops_per_cv_stage": ops, "kernel": k64,
+                                    "note": "FP64 lane operations (DFMA + DADD + DMUL, ncu) "
+                                            "per cell-velocity and stage against the "
+                                            "measured DFMA lane rate"}
 
     B_tile = tubes[0].launch_info()[0]
     from paper_1612_01287_gb300._lib import PACKED_TILE_CELLS
