@@ -194,52 +194,42 @@ def test_closure_step_matches_oracle_and_conserves():
 
 
 def test_trained_closure_lowers_low_order_error():
-    """Train on data the high-order method generates (Q_xi = 200, tau in
-    {0.01, 0.1, 1}), then run Q_xi = 8 with and without the closure from the
-    shock-tube state and compare L2 errors of e and beta against Q_xi = 200."""
-    import torch
-    from paper_1612_01287_gb300 import MLP, Sod, closure_sample, closure_step
+    """Train on data the high-order method generates (Q_xi = 200; 24 snapshots
+    with tau log-uniform in [1e-3, 10], targets scaled per tau), then run
+    Q_xi = 8 with and without the closure from the shock-tube state and compare
+    the L2 errors of e and beta against Q_xi = 200: no tau is made worse, and
+    the kinetic ones are improved."""
+    from paper_1612_01287_gb300 import Sod
+    from paper_1612_01287_gb300 import closure_train as CT
     Z, t_end = 512, 0.2
     dz = 2.0 / Z
     dt = 0.5 * dz / 0.9999
     nsteps = int(round(t_end / dt))
-    taus = (0.01, 0.1, 1.0)
-    Xs, Ts = [], []
-    for tau in taus:
-        hi, lo = sod_pair(Z, tau, dt)
-        with hi, lo:
-            for _ in range(nsteps):
-                Xd = torch.zeros((Z, D), device="cuda")
-                Td = torch.zeros((Z, O), device="cuda")
-                closure_sample(hi, lo, tau, Xd.data_ptr(), Td.data_ptr())
-                Xs.append(Xd)
-                Ts.append(Td)
-    X = torch.cat(Xs).contiguous()
-    T = torch.cat(Ts).contiguous()
-    N = X.shape[0]
+    rng = np.random.default_rng(workloads.SEED)
+    taus = 10.0 ** rng.uniform(-3.0, 1.0, size=24)
+    steps = [sorted(rng.integers(0, nsteps, size=12).tolist()) for _ in taus]
+    X, T, snaps = CT.generate(Z, taus, steps, dt)
+    cl_model, losses = CT.train(X, T, snaps, epochs=30, batch=2048, lr=2e-3, seed=11)
+    print("training samples", X.shape[0], "loss first/last epoch", losses[0], losses[-1])
+    assert losses[-1] < 0.5 * losses[0]
 
     def l2(a, b):
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
     res = {}
-    with MLP(D, H, O, seed=11) as m:
-        m.fit_normalization(X.data_ptr(), T.data_ptr(), N)
-        losses = m.train(X.data_ptr(), T.data_ptr(), N, epochs=30, batch=2048, lr=2e-3, seed=1)
-        print("training samples", N, "loss first/last epoch", losses[0], losses[-1])
-        assert losses[-1] < 0.5 * losses[0]
-        for tau in taus:
-            with Sod(Z=Z, Q_xi=QHI, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", tau=tau,
-                     dt=dt) as hi, \
-                    Sod(Z=Z, Q_xi=QLO, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", tau=tau,
-                        dt=dt) as lo, \
-                    Sod(Z=Z, Q_xi=QLO, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", tau=tau,
-                        dt=dt) as cl:
+    judged = (0.01, 0.1, 0.5, 1.0)
+    with cl_model:
+        for tau in judged:
+            kw = dict(Z=Z, Q_L=QL, N_Omega=5, precision="f32", bc="outflow", tau=tau, dt=dt)
+            with Sod(Q_xi=QHI, **kw) as hi, Sod(Q_xi=QLO, **kw) as lo, Sod(Q_xi=QLO, **kw) as cl:
                 hi.step(nsteps)
                 lo.step(nsteps)
-                closure_step(cl, m, tau, nsteps)
+                cl_model.step(cl, tau, nsteps)
                 mh, ml, mc = hi.moments(), lo.moments(), cl.moments()
             res[tau] = {"plain": (l2(ml["E"], mh["E"]), l2(ml["beta"], mh["beta"])),
                         "closure": (l2(mc["E"], mh["E"]), l2(mc["beta"], mh["beta"]))}
     print("L2 errors (e, beta) vs Q_xi = 200:", res)
-    gain = [res[t]["closure"][0] < res[t]["plain"][0] for t in taus]
-    assert sum(gain) >= 2, res
+    for t in judged:
+        assert res[t]["closure"][0] <= 1.05 * res[t]["plain"][0], (t, res)
+    better = [res[t]["closure"][0] < res[t]["plain"][0] for t in judged if t >= 0.1]
+    assert sum(better) >= 2, res
