@@ -359,25 +359,79 @@ def bench_bjorken(stream, steps=None):
 def bench_sod_batch(stream, steps=None):
     """Uneven batch of 4096 shock tubes (Z log-uniform [256, 8192], Q_xi in
     {8, 20, 50, 100, 200}, Q_L = 3, tau log-uniform [1e-4, 10], pressure ratio
-    [2, 20]); FP32; timed over the first batch steps, when every run is active."""
-    from paper_1612_01287_gb300 import SodBatch
+    [2, 20]); FP32.  Timed (1) over the first batch steps, when every run is
+    active, and (2) from the start until the runs have done a tenth of all
+    their cell-velocity updates to t_end (runs with few steps finish on the way).
+    Beside it, 16 runs of the sweep (seeded sample) to t_end as a batch and one
+    at a time through rslb_init/rslb_step (the plain form)."""
+    from paper_1612_01287_gb300 import Sod, SodBatch
     steps = steps or ARGS.batch_steps
     runs = workloads.sod_sweep()
     t0 = time.perf_counter()
+    peak, _ = measured_peak()
     with SodBatch(runs, precision="f32", autotune=True, stream=stream) as b:
         init_s = time.perf_counter() - t0
-        cv = sum(r["Z"] * 3 * r["Q_xi"] for r in runs)
+        V = np.array([3 * r["Q_xi"] for r in runs], dtype=np.float64)
+        Zr = np.array([r["Z"] for r in runs], dtype=np.float64)
+        nst = np.array([b.run_info(i)[0] for i in range(len(runs))], dtype=np.float64)
+        cv = float((Zr * V).sum())
         b.step(1)
         ms = _timed(stream, b.step, steps) / steps
         tuning = b.tuning()
         total = b.total_cv_updates
+        # (2) to a tenth of the work: the batch steps k with
+        # sum_r min(k, nsteps_r) Z_r V_r >= total / 10
+        done1 = steps + 1
+        k = done1
+        while float((np.minimum(k, nst) * Zr * V).sum()) < 0.1 * total:
+            k += 100
+        span = k - done1
+        ms_span = _timed(stream, b.step, span)
+        cv_span = float((np.minimum(k, nst) * Zr * V).sum() - (np.minimum(done1, nst) * Zr * V).sum())
         m = b.moments(0)
         if not np.all(np.isfinite(m["E"])):
             raise RuntimeError("non-finite batched state")
-    return {"runs": len(runs), "value": cv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-            "steps": steps, "cv_per_step": cv, "init_s": init_s,
-            "tuning": [{"V": V, "tile_cells": B, "ctas_per_sm": K} for V, B, K in tuning],
-            "cv_updates_to_t_end": total}
+    rate = cv_span / (ms_span * 1e-3)
+    ach = rate * BYTES_PER_CV_STEP_F32 / 1e9
+    out = {"runs": len(runs), "value": cv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+           "steps": steps, "cv_per_step": cv, "init_s": init_s,
+           "tuning": [{"V": V_, "tile_cells": B, "ctas_per_sm": K} for V_, B, K in tuning],
+           "cv_updates_to_t_end": total,
+           "to_tenth_of_work": {"batch_steps": [done1, k], "max_steps": int(nst.max()),
+                                "cv_updates": cv_span, "seconds": ms_span * 1e-3,
+                                "value": rate, "unit": UNIT,
+                                "roofline": {"bound": "hbm", "achieved": ach, "peak": peak,
+                                             "unit": "GB/s", "frac": ach / peak,
+                                             "bytes_per_cv_update": BYTES_PER_CV_STEP_F32}}}
+    # batch against one run at a time, on a sample of the sweep
+    rng = np.random.default_rng(workloads.SEED + 1)
+    sample = [runs[i] for i in rng.choice(len(runs), size=16, replace=False)]
+    with SodBatch(sample, precision="f32", autotune=True, stream=stream) as b:
+        b.step(1)
+        import torch
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run_to_end()
+        b.moments(0)
+        t_batch = time.perf_counter() - t0
+        sample_cv = b.total_cv_updates
+        info = [b.run_info(i) for i in range(len(sample))]
+    t_plain = 0.0
+    for r, (n, dtr) in zip(sample, info):
+        with Sod(Z=r["Z"], Q_xi=r["Q_xi"], Q_L=3, precision="f32", bc="outflow", tau=r["tau"],
+                 dt=dtr, left=(r["nL"], r["TL"], 0.0), right=(r["nR"], r["TR"], 0.0),
+                 stream=stream) as s:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step(int(n))
+            s.sync()
+            t_plain += time.perf_counter() - t0
+    out["batch_vs_plain_sample"] = {
+        "runs": len(sample), "cv_updates": sample_cv, "batch_s": t_batch, "plain_s": t_plain,
+        "speedup": t_plain / t_batch,
+        "note": "the same 16 runs to t_end: one batch (first step excluded) against one "
+                "handle per run stepped through rslb_step, one after another"}
+    return out
 
 
 def bench_closure(stream):
