@@ -104,9 +104,11 @@ class Closure:
 
 
 def train(X, T, snaps, hidden=64, epochs=40, batch=8192, lr=2e-3, seed=20161201, stream=None,
-          nodes=12):
+          nodes=12, max_z=20.0):
     """Scale each snapshot's targets by 1/s(tau) (in place), fit the fixed input
-    and output normalisation, train with Adam; returns (Closure, epoch losses)."""
+    and output normalisation (input scales widened so that no training input
+    exceeds max_z in normalised units), train with Adam; returns (Closure,
+    epoch losses)."""
     from . import MLP
     table = scale_table(snaps, nodes)
     for tau, r0, n, _ in snaps:
@@ -114,6 +116,13 @@ def train(X, T, snaps, hidden=64, epochs=40, batch=8192, lr=2e-3, seed=20161201,
     D, V = X.shape[1], T.shape[1]
     m = MLP(D, hidden, V, seed=seed, stream=stream)
     m.fit_normalization(X.data_ptr(), T.data_ptr(), X.shape[0])
+    # most cells are smooth, so the fitted input deviations are small and the
+    # cells at a discontinuity would reach hundreds of them: widen each
+    # column's scale so that no training input lies beyond max_z of it
+    mu, isd, osd = m.get_normalization()
+    amax = (X - X.new_tensor(mu)).abs().amax(0).cpu().numpy()
+    isd = np.minimum(isd, max_z / np.maximum(amax, 1e-30)).astype(np.float32)
+    m.set_normalization(mu, isd, osd)
     losses = m.train(X.data_ptr(), T.data_ptr(), X.shape[0], epochs=epochs, batch=batch, lr=lr,
                      seed=seed + 1)
     return Closure(m, table), losses

@@ -194,8 +194,9 @@ def test_closure_step_matches_oracle_and_conserves():
 
 
 def test_trained_closure_lowers_low_order_error():
-    """Train on data the high-order method generates (Q_xi = 200; 24 snapshots
-    with tau log-uniform in [1e-3, 10], targets scaled per tau), then run
+    """Train on data the high-order method generates (Q_xi = 200; 24 tubes with
+    tau log-uniform in [5e-3, 10] (dt = 2e-3 here; tau must exceed it), 12
+    snapshots each, targets scaled per tau), then run
     Q_xi = 8 with and without the closure from the shock-tube state and compare
     the L2 errors of e and beta against Q_xi = 200: no tau is made worse, and
     the kinetic ones are improved."""
@@ -206,7 +207,7 @@ def test_trained_closure_lowers_low_order_error():
     dt = 0.5 * dz / 0.9999
     nsteps = int(round(t_end / dt))
     rng = np.random.default_rng(workloads.SEED)
-    taus = 10.0 ** rng.uniform(-3.0, 1.0, size=24)
+    taus = 10.0 ** rng.uniform(np.log10(5e-3), 1.0, size=24)
     steps = [sorted(rng.integers(0, nsteps, size=12).tolist()) for _ in taus]
     X, T, snaps = CT.generate(Z, taus, steps, dt)
     cl_model, losses = CT.train(X, T, snaps, epochs=30, batch=2048, lr=2e-3, seed=11)
