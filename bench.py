@@ -462,6 +462,8 @@ def bench_closure(stream):
     cl_model, losses = CT.train(X, T, snaps, epochs=40, batch=8192, lr=2e-3, stream=stream)
     out["train_s"] = time.perf_counter() - t0
     out["loss_first_last"] = [float(losses[0]), float(losses[-1])]
+    out["explained_by_log10_tau"] = [[round(float(x), 3), round(float(y), 3)]
+                                     for x, y in zip(*cl_model.explained)]
     del X, T
 
     def l2(a, b):
@@ -487,7 +489,8 @@ def bench_closure(stream):
                 ml, t_lo = run(QLO, tau)
                 mc, t_cl = run(QLO, tau, closure=True)
                 err = lambda m: {"e": l2(m["E"], mh["E"]), "beta": l2(m["beta"], mh["beta"])}
-                row = {"plain_q8": err(ml), "closure_q8": err(mc),
+                row = {"closure_active": cl_model.active(tau),
+                       "plain_q8": err(ml), "closure_q8": err(mc),
                        "wall_s": {"q200_plain": t_hi, "q8_plain": t_lo, "q8_closure": t_cl}}
                 ok = lambda e: e["e"] <= thr and e["beta"] <= thr
                 eq = {"threshold": thr, "closure_reaches": ok(row["closure_q8"]),

@@ -14,6 +14,12 @@ divided by a scale s(tau), interpolated log-log from the root-mean-square
 targets of the snapshots, and the network learns the scaled targets: every tau
 range weighs the same in the loss.  When the closure is applied at a given tau,
 the network's output scale is multiplied by s(tau) for that call.
+
+After training, the part of each snapshot's scaled one-step target that the
+network reproduces, 1 - |T - net(X)|^2 / |T|^2, is binned in log tau like the
+scale.  Where that explained fraction is below a gate (one half), the network
+does not know the one-step correction at that tau and the low-order method
+runs without it: the plain method is the fallback.
 """
 import math
 
@@ -77,15 +83,48 @@ def scale_at(tau, table):
     return float(math.exp(np.interp(math.log10(tau), xs, ys)))
 
 
-class Closure:
-    """A trained network and its target scale table; step() applies it."""
+def explained_table(T, Y, snaps, nodes=12):
+    """(log10 tau nodes, explained fraction): 1 - |T - Y|^2/|T|^2 of each
+    snapshot's rows, averaged in the log-tau bins of scale_table."""
+    lt = np.array([math.log10(s[0]) for s in snaps])
+    ex = []
+    for _, r0, n, _ in snaps:
+        t, y = T[r0:r0 + n].double(), Y[r0:r0 + n].double()
+        den = float((t * t).sum().item())
+        ex.append(1.0 - float(((t - y) ** 2).sum().item()) / den if den > 0 else 0.0)
+    ex = np.array(ex)
+    edges = np.linspace(lt.min(), lt.max() + 1e-12, nodes + 1)
+    xs, ys = [], []
+    for a, b in zip(edges[:-1], edges[1:]):
+        m = (lt >= a) & (lt < b)
+        if m.any():
+            xs.append(float(lt[m].mean()))
+            ys.append(float(ex[m].mean()))
+    return np.array(xs), np.array(ys)
 
-    def __init__(self, mlp, table):
+
+class Closure:
+    """A trained network, its target scale table and its explained-fraction
+    table; step() applies it where the explained fraction reaches the gate
+    and runs the plain low-order method elsewhere."""
+
+    def __init__(self, mlp, table, explained=None, gate=0.5):
         self.mlp = mlp
         self.table = table
+        self.explained = explained
+        self.gate = gate
+
+    def active(self, tau):
+        if self.explained is None:
+            return True
+        xs, ys = self.explained
+        return float(np.interp(math.log10(tau), xs, ys)) >= self.gate
 
     def step(self, lo, tau, nsteps):
         from . import closure_step
+        if not self.active(tau):
+            lo.step(nsteps)
+            return
         mu, isd, osd = self.mlp.get_normalization()
         self.mlp.set_normalization(mu, isd, osd * np.float32(scale_at(tau, self.table)))
         try:
@@ -108,7 +147,8 @@ def train(X, T, snaps, hidden=64, epochs=40, batch=8192, lr=2e-3, seed=20161201,
     """Scale each snapshot's targets by 1/s(tau) (in place), fit the fixed input
     and output normalisation (input scales widened so that no training input
     exceeds max_z in normalised units), train with Adam; returns (Closure,
-    epoch losses)."""
+    epoch losses); the Closure carries the explained-fraction table."""
+    import torch
     from . import MLP
     table = scale_table(snaps, nodes)
     for tau, r0, n, _ in snaps:
@@ -125,4 +165,9 @@ def train(X, T, snaps, hidden=64, epochs=40, batch=8192, lr=2e-3, seed=20161201,
     m.set_normalization(mu, isd, osd)
     losses = m.train(X.data_ptr(), T.data_ptr(), X.shape[0], epochs=epochs, batch=batch, lr=lr,
                      seed=seed + 1)
-    return Closure(m, table), losses
+    Y = torch.empty_like(T)
+    m.forward(X.data_ptr(), X.shape[0], Y.data_ptr())
+    torch.cuda.synchronize()
+    explained = explained_table(T, Y, snaps, nodes)
+    del Y
+    return Closure(m, table, explained), losses

@@ -80,9 +80,14 @@ def sod_qxi_sweep(etas, qxis, Z=1000, t_end=0.5, dt=5e-4, Q_L=2, q_ref=500, n_om
     from . import SodBatch
     runs = []
     for es in etas:
+        # explicit RK3 needs dt below ~2.5 tau; the smallest tau of the tube is
+        # tau_AW0 / max T (the log factor is 1 in both chambers), so tubes
+        # with a smaller tau than 2 dt take an even division of t_end instead
+        tau_min = tau_coef * es / max(left[1], right[1])
+        dt_r = dt if dt <= 0.5 * tau_min else t_end / math.ceil(t_end / (0.5 * tau_min))
         for j, q in enumerate(list(qxis) + [q_ref]):
             nom = n_omega_ref if j == len(qxis) else min(q - 1, 5)
-            runs.append(dict(Z=Z, Q_xi=int(q), t_end=t_end, dt=dt, tau_mode="etas",
+            runs.append(dict(Z=Z, Q_xi=int(q), t_end=t_end, dt=dt_r, tau_mode="etas",
                              tau_AW0=tau_coef * es, lambda_ref=lambda_ref, N_Omega=nom,
                              nL=left[0], TL=left[1], nR=right[0], TR=right[1]))
     with SodBatch(runs, Q_L=Q_L, precision=precision, bc="fixed_eq", z_min=z_min, z_max=z_max,
