@@ -308,7 +308,10 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
   T* tile = reinterpret_cast<T*>(smem_raw + lay.tile);
   T* outb = (nseg > 1) ? reinterpret_cast<T*>(smem_raw + lay.outb) : nullptr;
   double* msum = reinterpret_cast<double*>(smem_raw + lay.msum);
-  double* cell = reinterpret_cast<double*>(smem_raw + lay.cell);
+  // per-cell results of the Landau phase for the coefficient phase, [8][B]
+  // values of the kernel's type (the FP32 kernel takes its coefficient
+  // arithmetic in FP32)
+  T* cellT = reinterpret_cast<T*>(smem_raw + lay.cell);
   T* coef = reinterpret_cast<T*>(smem_raw + lay.coef);
   T* gco = reinterpret_cast<T*>(smem_raw + lay.gco);
   const int MP = coef_pitch<T>(g.nm);
@@ -433,15 +436,15 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
       const int c = tid;
       LandauOut Lo = landau_factored(msum[c], msum[B + c], msum[2 * B + c], msum[3 * B + c],
                                      msum[4 * B + c]);
-      double g0 = 0.0, g1 = 0.0;
+      T g0 = T(0), g1 = T(0);
       if (!Lo.ok) {
         if (s0 + c < g.Z) report_error(err, 6, s0 + c);
         Lo.n = 1.0; Lo.T = 1.0; Lo.beta = 0.0; Lo.gamma = 1.0; Lo.u = 0.0;
       } else if (g.tau_mode == kTauEtas) {
         const double tau = g.tau_AW0 / Lo.T *
                            (1.0 - 0.25 * log(Lo.n / (Lo.T * Lo.T * Lo.T) * g.lambda_ref));
-        g0 = Lo.gamma / tau;
-        g1 = Lo.gamma * Lo.beta / tau;
+        g0 = T(Lo.gamma / tau);
+        g1 = T(Lo.gamma * Lo.beta / tau);
       } else if constexpr (sizeof(T) == 4) {
         const float itau = 1.f / float(g.tau);
         g0 = float(Lo.gamma) * itau;
@@ -454,26 +457,26 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
         // FP32 from here on: the coefficients are computed in FP32
         const float u = float(Lo.u);
         const float A = asinhf(u);
-        cell[0 * B + c] = Lo.n;
-        cell[1 * B + c] = Lo.T;
-        cell[2 * B + c] = u;
-        cell[3 * B + c] = A;
-        cell[4 * B + c] = (u > 0.f) ? A / u : 1.f;
-        cell[5 * B + c] = u * u / (float(Lo.gamma) + 1.f);  // 2 sinh^2(A/2) = gamma - 1
+        cellT[0 * B + c] = float(Lo.n);
+        cellT[1 * B + c] = float(Lo.T);
+        cellT[2 * B + c] = u;
+        cellT[3 * B + c] = A;
+        cellT[4 * B + c] = (u > 0.f) ? A / u : 1.f;
+        cellT[5 * B + c] = u * u / (float(Lo.gamma) + 1.f);  // 2 sinh^2(A/2) = gamma - 1
       } else {
         const double A = asinh(Lo.u);
         const double sh = sinh(0.5 * A);
-        cell[0 * B + c] = Lo.n;
-        cell[1 * B + c] = Lo.T;
-        cell[2 * B + c] = Lo.u;
-        cell[3 * B + c] = A;
-        cell[4 * B + c] = (Lo.u > 0.0) ? A / Lo.u : 1.0;
-        cell[5 * B + c] = 2.0 * sh * sh;
+        cellT[0 * B + c] = Lo.n;
+        cellT[1 * B + c] = Lo.T;
+        cellT[2 * B + c] = Lo.u;
+        cellT[3 * B + c] = A;
+        cellT[4 * B + c] = (Lo.u > 0.0) ? A / Lo.u : 1.0;
+        cellT[5 * B + c] = 2.0 * sh * sh;
       }
-      cell[6 * B + c] = (Lo.beta < 0.0) ? -1.0 : 1.0;
-      cell[7 * B + c] = Lo.ok ? 1.0 : 0.0;
-      gco[2 * c] = T(g0);
-      gco[2 * c + 1] = T(g1);
+      cellT[6 * B + c] = (Lo.beta < 0.0) ? T(-1) : T(1);
+      cellT[7 * B + c] = Lo.ok ? T(1) : T(0);
+      gco[2 * c] = g0;
+      gco[2 * c + 1] = g1;
     }
     __syncthreads();
 
@@ -482,10 +485,10 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
       constexpr int G = (256 / B) < 32 ? (256 / B) : 32;
       const int c = tid / G, q = tid - c * G;
       if (c < B) {
-        const double ud = cell[2 * B + c];
-        const T A = T(cell[3 * B + c]), sh2 = T(cell[5 * B + c]);
-        const T uinv = (ud > 0.0) ? T(1.0 / ud) : T(0);
-        const bool at_rest = !(ud > 0.0);
+        const T ud = cellT[2 * B + c];
+        const T A = cellT[3 * B + c], sh2 = cellT[5 * B + c];
+        const T uinv = (ud > T(0)) ? T(1) / ud : T(0);
+        const bool at_rest = !(ud > T(0));
         T J3[kMaxM], J4[kMaxM];
 #pragma unroll
         for (int m = 0; m < kMaxM; ++m) { J3[m] = T(0); J4[m] = T(0); }
@@ -504,10 +507,9 @@ __device__ __forceinline__ void sod_tile(const T* __restrict__ fin, const T* __r
             }
         if (q == 0) {
           // c''_{k,m} = sgn^m (2m+1)/2 (n r/4) [J3_m + (3 - x_k)(J3_m - theta J4_m)]
-          const double ok = cell[7 * B + c];
-          const T fac = T(ok * cell[0 * B + c] * cell[4 * B + c] * 0.25);
-          const T theta = T(cell[1 * B + c]);
-          const T sgn = T(cell[6 * B + c]);
+          const T fac = cellT[7 * B + c] * cellT[0 * B + c] * cellT[4 * B + c] * T(0.25);
+          const T theta = cellT[1 * B + c];
+          const T sgn = cellT[6 * B + c];
           T sm = fac;
 #pragma unroll
           for (int m = 0; m < kMaxM; ++m) {

@@ -230,7 +230,7 @@ def test_trained_closure_lowers_low_order_error():
     snapshots each, targets scaled per tau), then run
     Q_xi = 8 with and without the closure from the shock-tube state and compare
     the L2 errors of e and beta against Q_xi = 200: no tau is made worse (where
-    the network explains less than half of the one-step target the plain
+    the network explains less than 0.8 of the one-step target the plain
     low-order method runs), and the kinetic ones are improved."""
     from paper_1612_01287_gb300 import Sod
     from paper_1612_01287_gb300 import closure_train as CT
