@@ -359,6 +359,9 @@ struct rslb_bjorken {
   double* mp[2];
   int mp_cur;  // which moment buffer describes the state (F0)
   float* ytmp;
+  long long* step_dev;           // steps taken, read by the stage kernels for their times
+  cudaGraphExec_t tc_graph[2];   // kTcGraphSteps steps, per parity of mp_cur at the start
+  bool tc_graph_failed;
 };
 
 namespace {
@@ -367,9 +370,12 @@ void bj_free(rslb_bjorken* b) {
   if (!b) return;
   void* ptrs[] = {b->state, b->kpool, b->npool, b->kpc, b->blocks, b->qtab, b->roff, b->xoff, b->rq,
                   b->tau_aw0, b->gas, b->user, b->xk, b->wk, b->KL, b->err, b->out_dev,
-                  b->tcblocks, b->kimg, b->F1, b->F2, b->mp[0], b->mp[1], b->ytmp};
+                  b->tcblocks, b->kimg, b->F1, b->F2, b->mp[0], b->mp[1], b->ytmp,
+                  b->step_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (cudaGraphExec_t g : b->tc_graph)
+    if (g) cudaGraphExecDestroy(g);
   delete b;
 }
 
@@ -622,7 +628,8 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
                 cudaMalloc(&b->F1, sb) != cudaSuccess || cudaMalloc(&b->F2, sb) != cudaSuccess ||
                 cudaMalloc((void**)&b->ytmp, sb) != cudaSuccess ||
                 cudaMalloc((void**)&b->mp[0], sizeof(double) * 8 * nruns) != cudaSuccess ||
-                cudaMalloc((void**)&b->mp[1], sizeof(double) * 8 * nruns) != cudaSuccess))
+                cudaMalloc((void**)&b->mp[1], sizeof(double) * 8 * nruns) != cudaSuccess ||
+                cudaMalloc((void**)&b->step_dev, sizeof(long long)) != cudaSuccess))
       rc = set_error(RSLB_ERR_ALLOC, "rslb_bjorken_init: cannot allocate the tensor-core buffers");
   }
   if (rc) {
@@ -631,6 +638,7 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
   }
   cudaStream_t st = b->stream;
   cudaMemsetAsync(b->err, 0, 2 * sizeof(int), st);
+  if (b->step_dev) cudaMemsetAsync(b->step_dev, 0, sizeof(long long), st);
   // K^P per distinct Q, K^L, initial state
   for (size_t i = 0; i < qvals.size() && o->kp_mode != RSLB_KP_TF32X3; ++i) {
     const int Q = qvals[i];
@@ -681,6 +689,66 @@ extern "C" int rslb_bjorken_init(rslb_bjorken** out, const rslb_bjorken_run* run
   return RSLB_OK;
 }
 
+namespace {
+
+// Steps of a graph of the tensor-core path: an even count, so that the moment
+// buffers are back in their starting roles at its end.
+constexpr int kTcGraphSteps = 2;
+
+// Enqueue nsteps RK3 steps of the tensor-core path: three stage launches each
+// (stage times from the device step counter, Tab. II) and the counter update.
+cudaError_t bj_tc_enqueue(rslb_bjorken* b, int nsteps) {
+  float* F[3] = {(float*)b->state, (float*)b->F1, (float*)b->F2};
+  cudaError_t e = cudaSuccess;
+  for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+    for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+      BjTcArgs a{};
+      a.blocks = b->tcblocks;
+      a.kimg = b->kimg;
+      a.npool = b->npool;
+      a.tau_aw0 = b->tau_aw0;
+      a.gas = b->gas;
+      a.xk = b->xk;
+      a.wk = b->wk;
+      a.KL = b->KL;
+      a.QL = b->QL;
+      a.stage = stage;
+      a.Fin = F[stage];
+      a.Fn = F[0];
+      a.Fout = F[(stage + 1) % 3];
+      a.mp_in = b->mp[b->mp_cur];
+      a.mp_out = b->mp[1 - b->mp_cur];
+      a.dout = nullptr;
+      a.step = b->step_dev;
+      a.tau0 = b->tau0;
+      a.dtau = b->dtau;
+      a.err = b->err;
+      e = bj_tc_stage_launch(a, b->ntc, b->tc_smem, b->stream);
+      b->mp_cur = 1 - b->mp_cur;
+    }
+    if (e == cudaSuccess) e = bj_step_count_launch(b->step_dev, b->stream);
+  }
+  return e;
+}
+
+// Capture kTcGraphSteps steps for the current parity of mp_cur (non-default
+// streams only: the legacy default stream cannot be captured).
+cudaError_t bj_tc_build_graph(rslb_bjorken* b) {
+  const int par = b->mp_cur;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t le = bj_tc_enqueue(b, kTcGraphSteps);
+  e = cudaStreamEndCapture(b->stream, &g);
+  if (le != cudaSuccess) e = le;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->tc_graph[par], g, 0);
+  if (g) cudaGraphDestroy(g);
+  b->mp_cur = par;  // capture enqueued nothing
+  return e;
+}
+
+}  // namespace
+
 extern "C" int rslb_bjorken_step(rslb_bjorken* b, int nsteps) {
   clear_error();
   if (!b || nsteps < 0) return set_error(RSLB_ERR_ARG, "rslb_bjorken_step: bad arguments");
@@ -688,36 +756,25 @@ extern "C" int rslb_bjorken_step(rslb_bjorken* b, int nsteps) {
   const double tau_start = b->tau0 + b->steps * b->dtau;
   cudaError_t e;
   if (b->kp_mode == RSLB_KP_TF32X3) {
-    float* F[3] = {(float*)b->state, (float*)b->F1, (float*)b->F2};
-    const double cst[3] = {0.0, 1.0, 0.5};
     e = cudaSuccess;
-    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
-      const double tn = tau_start + n * b->dtau;
-      for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
-        BjTcArgs a{};
-        a.blocks = b->tcblocks;
-        a.kimg = b->kimg;
-        a.npool = b->npool;
-        a.tau_aw0 = b->tau_aw0;
-        a.gas = b->gas;
-        a.xk = b->xk;
-        a.wk = b->wk;
-        a.KL = b->KL;
-        a.QL = b->QL;
-        a.stage = stage;
-        a.Fin = F[stage];
-        a.Fn = F[0];
-        a.Fout = F[(stage + 1) % 3];
-        a.mp_in = b->mp[b->mp_cur];
-        a.mp_out = b->mp[1 - b->mp_cur];
-        a.dout = nullptr;
-        a.tau = tn + cst[stage] * b->dtau;
-        a.dtau = b->dtau;
-        a.err = b->err;
-        e = bj_tc_stage_launch(a, b->ntc, b->tc_smem, b->stream);
-        b->mp_cur = 1 - b->mp_cur;
+    int rest = nsteps;
+    if (b->stream != nullptr && nsteps >= kTcGraphSteps && !b->tc_graph_failed) {
+      if (!b->tc_graph[b->mp_cur]) {
+        e = bj_tc_build_graph(b);
+        if (e != cudaSuccess) {
+          // plain launches from here on (e.g. the caller's stream is being captured)
+          b->tc_graph[b->mp_cur] = nullptr;
+          b->tc_graph_failed = true;
+          cudaGetLastError();
+          e = cudaSuccess;
+        }
+      }
+      while (b->tc_graph[b->mp_cur] && rest >= kTcGraphSteps && e == cudaSuccess) {
+        e = cudaGraphLaunch(b->tc_graph[b->mp_cur], b->stream);
+        rest -= kTcGraphSteps;
       }
     }
+    if (e == cudaSuccess && rest > 0) e = bj_tc_enqueue(b, rest);
     if (e != cudaSuccess) return cuda_error(e, "rslb_bjorken_step: launch");
     b->steps += nsteps;
     return RSLB_OK;

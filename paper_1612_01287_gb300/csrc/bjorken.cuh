@@ -111,6 +111,8 @@ struct BjTcArgs {
   double* mp_out;         // moments of Fout
   float* dout;            // stage -1 only
   double tau, dtau;       // stage time and step
+  const long long* step;  // if set: the stage time is tau0 + (*step + c_stage) dtau, with
+  double tau0;            // c = 0, 1, 1/2 (Tab. II), read on the device (graph replays)
   int* err;
   int withhold_ready;     // failure-handling self-test: the workers never
                           // signal that their operand tiles are ready
@@ -122,6 +124,7 @@ constexpr int kTcMaxCols = 80;
 cudaError_t bj_tc_set_attributes();
 size_t bj_tc_smem_bytes(int nc, int R);
 cudaError_t bj_tc_stage_launch(const BjTcArgs& a, int nblocks, size_t smem, cudaStream_t st);
+cudaError_t bj_step_count_launch(long long* step, cudaStream_t st);
 cudaError_t bj_tc_image_launch(int Q, const double* xw, const double* kc, float* img,
                                cudaStream_t st);
 cudaError_t bj_tc_moments_launch(int nruns, int QL, const int* rq, const long long* roff,

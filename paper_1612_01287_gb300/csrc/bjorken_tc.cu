@@ -470,7 +470,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) bj_tc_stage_kernel(BjTcArgs a) 
   // ---- epilogue (worker warps): rows j1 = i and j2 = Q-1-i per thread ----
   // (K f)_{j1} = (Y_E + Y_O)/2, (K f)_{j2} = (Y_E - Y_O)/2 (Y_O = 0 past h)
   if (warp < 4) {
-    const float itau = float(1.0 / a.tau), dt = float(a.dtau);
+    const double tau_s =
+        a.step ? a.tau0 + ((double)*a.step + (a.stage == 1 ? 1.0 : (a.stage == 2 ? 0.5 : 0.0))) *
+                              a.dtau
+               : a.tau;
+    const float itau = float(1.0 / tau_s), dt = float(a.dtau);
     const float ca = a.stage == 1 ? 0.75f : 1.f / 3.f, cb = a.stage == 1 ? 0.25f : 2.f / 3.f;
     const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
     const float* Fin = a.Fin + blk.soff;
@@ -666,6 +670,13 @@ cudaError_t bj_tc_set_attributes() {
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+__global__ void bj_step_count_kernel(long long* step) { *step += 1; }
+
+cudaError_t bj_step_count_launch(long long* step, cudaStream_t st) {
+  bj_step_count_kernel<<<1, 1, 0, st>>>(step);
+  return cudaGetLastError();
 }
 
 cudaError_t bj_tc_stage_launch(const BjTcArgs& a, int nblocks, size_t smem, cudaStream_t st) {

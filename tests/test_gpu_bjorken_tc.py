@@ -84,6 +84,28 @@ def test_seeded_workload_sample_tf32x3():
         assert v <= 1e-5, (k, e)
 
 
+def test_graph_replayed_steps_match_plain_launches():
+    """On a non-default stream the tensor-core steps run as graphs of two
+    steps (one per parity of the moment buffers), the odd remainder as plain
+    launches, the stage times read from a device step counter: uneven step
+    counts give bitwise the states of plain launches on the default stream."""
+    import torch
+    from paper_1612_01287_gb300 import Bjorken
+    Qs, gases, taus = MIXED
+    st = torch.cuda.Stream()
+    kw = dict(Q_L=3, precision="f32", kp_mode="tf32x3", dtau=1e-2)
+    with Bjorken(Qs, gases, taus, **kw) as a, Bjorken(Qs, gases, taus, stream=st, **kw) as b:
+        a.step(18)
+        for n in (7, 6, 1, 4):
+            b.step(n)
+        st.synchronize()
+        fa, fb = a.get_state(), b.get_state()
+        ra, rb = a.read(), b.read()
+    assert np.array_equal(fa, fb)
+    for k in ra:
+        assert np.array_equal(ra[k], rb[k]), k
+
+
 def test_tf32x3_tracks_simt_fp32():
     """The two FP32 contraction paths agree on a long ideal-gas run."""
     from paper_1612_01287_gb300 import Bjorken
