@@ -147,8 +147,9 @@ typedef struct rslb_handle rslb_handle;
  * rslb_destroy.
  * Errors: RSLB_ERR_ARG (bad cfg), RSLB_ERR_CFL (max|xi| dt/dz >= 1),
  * RSLB_ERR_STIFF (RSLB_TAU_CONST and dt >= tau), RSLB_ERR_UNSUPPORTED
- * (V = Q_xi*Q_L too large for one tile of 16 (FP32) or 8 (FP64) cells),
- * RSLB_ERR_ALLOC, RSLB_ERR_CUDA,
+ * (V = Q_xi*Q_L too large for one tile of 16 (FP32) or 8 (FP64) cells, or
+ * V * ldz >= 2^31 populations in one buffer, ldz = Z rounded up to a multiple
+ * of 32; checked before any device work), RSLB_ERR_ALLOC, RSLB_ERR_CUDA,
  * RSLB_ERR_NONPHYSICAL (an initial state with n <= 0, T <= 0 or |beta| >= 1).
  */
 int rslb_init(rslb_handle** h, const rslb_config* cfg, void* stream);

@@ -329,6 +329,10 @@ extern "C" int rslb_init(rslb_handle** out, const rslb_config* cfg, void* stream
   if (c.bc == RSLB_BC_PERIODIC && c.Z < 6)
     return set_error(RSLB_ERR_ARG, "rslb_init: periodic domains need Z >= 6");
   const int Qx = c.Q_xi, QL = c.Q_L, V = Qx * QL, nm = c.N_Omega + 1;
+  // the kernels index a population buffer [V][ldz] with 32-bit offsets in places
+  if ((long long)V * (((long long)c.Z + 31) / 32 * 32) >= (1LL << 31))
+    return set_error(RSLB_ERR_UNSUPPORTED,
+                     "rslb_init: V x Z = %d x %d populations per buffer (limit 2^31)", V, c.Z);
   std::vector<double> xj(Qx), wj(Qx), xk(QL), wk(QL), glt(kAeqTable), glw(kAeqTable);
   gauss_legendre_host(Qx, xj.data(), wj.data());
   gauss_laguerre2_host(QL, xk.data(), wk.data());

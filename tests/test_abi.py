@@ -74,6 +74,7 @@ def test_quadrature_rejects_bad_orders(lib):
     (dict(dt=0.1), 2),            # CFL >= 1
     (dict(dt=2e-3, tau=1e-3), 3),  # dt >= tau: stiff
     (dict(bc="periodic", Z=4), 1),
+    (dict(Z=4_000_000, Q_xi=200, Q_L=3, dt=1e-7), 7),  # V x ldz >= 2^31 populations
 ])
 def test_host_side_validation(lib, kw, code):
     """Argument errors are rejected on the host before any device work."""
