@@ -57,3 +57,24 @@ def test_traffic_key_ignores_header_comments(tmp_path, monkeypatch):
     kern = files["paper_1612_01287_gb300/csrc/sod32.cu"]
     kern.write_text(kern.read_text() + "\n")
     assert bench.source_sha("sod32_stage_kernel") != base
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` runs the FP64 oracle on the host cores (no
+    GPU, no library build) and prints one JSON line with the arm's keys."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    assert d["metric"] == "cell-velocity updates/s" and d["higher_is_better"] is True
