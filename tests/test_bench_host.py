@@ -78,3 +78,13 @@ def test_reference_arm_prints_one_contract_line():
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     assert d["metric"] == "cell-velocity updates/s" and d["higher_is_better"] is True
+
+
+def test_recorded_counters_follow_the_current_kernel_sources():
+    """Every ncu record the bench reads (DRAM traffic, FP64 operation counts) was
+    taken on the kernel source as it stands; a changed kernel voids its record,
+    so a stale one would silently drop a roofline key from the bench line."""
+    import json
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for kernel, rec in d.items():
+        assert rec["source_sha"] == bench.source_sha(kernel), kernel
